@@ -1,0 +1,272 @@
+/*
+ * lqs.h -- C ABI of the GB300 state-vector gate engine.
+ *
+ * The engine applies quantum gates to a 2^n-amplitude state vector held in one
+ * GPU's HBM, with kernels chosen by gate class and qubit index, after the
+ * index-dependent, gate-specific strategy of arxiv 2508.13615 (Sec. 2):
+ * every gate uses only the nonzero entries of its matrix, and how a gate runs
+ * depends on which qubit indices it touches.  On one GPU the paper's
+ * local/non-local split becomes "inside a shared-memory tile" versus "strided
+ * HBM passes".
+ *
+ * Conventions
+ *   - Qubit q is bit q of the amplitude index (stride 2^q).  The paper numbers
+ *     qubits from 0 and pairs a gate on target q_T with the amplitude 2^q_T
+ *     away (rank distance 2^(q_T-L), Sec. 2, Fig. 1a/1b), so qubit 0 is the
+ *     least significant bit.
+ *   - Amplitudes are interleaved complex numbers (re, im): complex64 is two
+ *     float32, complex128 two float64.  The state is one contiguous array of
+ *     2^n amplitudes, 256-byte aligned.
+ *   - A gate's wires are listed control(s) first, target last (CNOT = {c, t},
+ *     Toffoli = {c1, c2, t}).  A user matrix (U2: 2x2, U4: 4x4) is row-major
+ *     interleaved complex128 on the host; its first listed wire is the most
+ *     significant bit of the row/column index.
+ *   - Gate definitions follow the public PennyLane operator definitions, which
+ *     the paper's simulator extends (Sec. 1): RX/RY/RZ(t) = exp(-i t P / 2),
+ *     PhaseShift(p) = diag(1, e^{ip}), Rot(a, b, c) = RZ(c) RY(b) RZ(a),
+ *     ControlledPhaseShift(p) = diag(1, 1, 1, e^{ip}).
+ *
+ * Errors: every call returns LQS_OK (0) or a negative LQS_ERR_* code and never
+ * throws across the ABI; lqs_last_error() returns a message for the calling
+ * thread.  Arguments are validated before any work is enqueued: a call that
+ * fails validation leaves the state untouched.
+ *
+ * Streams: every call on a state is enqueued on the CUDA stream given to
+ * lqs_sv_alloc (a cudaStream_t; NULL = the legacy default stream) and is
+ * asynchronous unless it returns host values (lqs_expval, lqs_norm2,
+ * lqs_adjoint_grad, lqs_batch_run, lqs_sv_copy_to_host, lqs_sv_sync).
+ *
+ * Arithmetic: complex64 states use float32 gate arithmetic; complex128 states
+ * use double-float arithmetic on the float32 pipes (two float32 per double,
+ * about 2^-46 relative error per operation for magnitudes in [2^-80, 2^127),
+ * absolute error below 2^-125 under it), because GB300's float64 units run at
+ * a small fraction of its float32 rate.  In that mode amplitudes with
+ * magnitude below 2^-103 are treated as zero and magnitudes must stay below
+ * 2^127; LQS_ARITH_F64 selects native float64 instead.  Norms, expectation
+ * values and gradient inner products accumulate in float64 for both dtypes.
+ */
+#ifndef LQS_ABI_H_INCLUDED
+#define LQS_ABI_H_INCLUDED
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LQS_API __attribute__((visibility("default")))
+#else
+#define LQS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define LQS_OK 0
+#define LQS_ERR_ARG (-1)          /* invalid argument: wires, counts, sizes, null pointers      */
+#define LQS_ERR_OOM (-2)          /* device memory could not be allocated                        */
+#define LQS_ERR_CUDA (-3)         /* a CUDA call or kernel launch failed                         */
+#define LQS_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up (the kernel returned)    */
+#define LQS_ERR_UNSUPPORTED (-5)  /* the request is valid but not supported (no GPU, dtype ...)  */
+
+typedef enum { LQS_C64 = 0, LQS_C128 = 1 } lqs_dtype;
+
+/* Gate set: Pauli-X/Z and CNOT (Sec. 2, Sec. 3.1), Hadamard and controlled
+ * phase / R_k (Sec. 3.2, Fig. 5a, Fig. 6a), DoubleExcitation's building
+ * blocks and parametrised rotations for variational circuits (Listing 1),
+ * Toffoli (the 8x8 case of Sec. 2), and generic 2x2 / 4x4 unitaries (the
+ * "general approach" of Sec. 3.1). */
+typedef enum {
+  LQS_X = 0, LQS_Y = 1, LQS_Z = 2, LQS_H = 3, LQS_S = 4, LQS_T = 5,
+  LQS_RX = 6, LQS_RY = 7, LQS_RZ = 8, LQS_PHASE = 9, LQS_ROT = 10,
+  LQS_CNOT = 11, LQS_CZ = 12, LQS_SWAP = 13, LQS_CPHASE = 14, LQS_CRY = 15,
+  LQS_TOFFOLI = 16, LQS_U2 = 17, LQS_U4 = 18,
+  LQS_NUM_GATES = 19
+} lqs_gate;
+
+/* c128 arithmetic selection (lqs_fuse_cfg.arith and lqs_set_arith). */
+typedef enum { LQS_ARITH_AUTO = 0, LQS_ARITH_F64 = 1, LQS_ARITH_DF = 2 } lqs_arith;
+
+typedef struct lqs_sv lqs_sv; /* opaque state-vector handle */
+
+/* One gate of a circuit.  param_idx indexes the caller's parameter array
+ * (first of the gate's parameters; -1 when the gate has none).  matrix: U2/U4
+ * only, host pointer, row-major interleaved complex128, read during the call. */
+typedef struct {
+  int32_t gate;
+  int32_t wires[3];
+  int32_t param_idx;
+  int32_t inverse; /* nonzero: apply the adjoint U^dagger */
+  const double* matrix;
+} lqs_op;
+
+/* coeff * prod_q sigma_q with sigma_q chosen by bit q of (x_mask, z_mask):
+ * I = (0,0), X = (1,0), Z = (0,1), Y = (1,1). */
+typedef struct {
+  double coeff;
+  uint64_t x_mask;
+  uint64_t z_mask;
+} lqs_pauli;
+
+/* Fusion / tiling controls; all zero = automatic (autotuned per n and dtype). */
+typedef struct {
+  int32_t tile_qubits; /* k: qubits per shared-memory tile (2^k amplitudes), 0 = auto */
+  int32_t low_qubits;  /* b: contiguous low qubits always in a tile (coalescing), 0 = auto */
+  int32_t arith;       /* lqs_arith, c128 only */
+  int32_t max_ops;     /* cap on gates per fused segment, 0 = no cap beyond the program size */
+} lqs_fuse_cfg;
+
+/* ---- state vectors ----------------------------------------------------------- */
+
+/* Create a handle for an n-qubit state (1 <= n <= 36).
+ * device_ptr: caller-owned device memory of at least 2^n amplitudes, 256-byte
+ *   aligned (for example a torch tensor's data_ptr()); the caller keeps
+ *   ownership and must keep it alive until lqs_sv_free.  NULL: the library
+ *   allocates it with cudaMalloc (LQS_ERR_OOM on failure) and owns it.
+ * cuda_stream: the cudaStream_t every call on this state is ordered on.
+ * The contents are not initialised.  *out receives the handle. */
+LQS_API int lqs_sv_alloc(int n_qubits, int dtype, void* device_ptr, void* cuda_stream, lqs_sv** out);
+
+/* Release the handle, its scratch buffers and, when the library allocated the
+ * state, the state itself (after the stream drains).  NULL is accepted. */
+LQS_API int lqs_sv_free(lqs_sv* sv);
+
+/* Device pointer, qubit count and dtype of a handle. */
+LQS_API int lqs_sv_info(const lqs_sv* sv, void** device_ptr, int* n_qubits, int* dtype);
+
+/* |x>: amplitude x = 1, all others 0 (x < 2^n).  Asynchronous. */
+LQS_API int lqs_sv_set_basis(lqs_sv* sv, uint64_t x);
+
+/* Copy 2^n amplitudes (the state's dtype, interleaved) from host memory.
+ * Enqueued on the stream; pinned host memory makes it asynchronous, so the
+ * host buffer must stay unchanged until the stream passes the copy. */
+LQS_API int lqs_sv_copy_from_host(lqs_sv* sv, const void* host);
+
+/* Copy the state to host memory; returns when the data is in `host`. */
+LQS_API int lqs_sv_copy_to_host(const lqs_sv* sv, void* host);
+
+/* Wait for all work enqueued on the state's stream; reports deferred kernel
+ * errors (LQS_ERR_CUDA) and device-side wait timeouts (LQS_ERR_TIMEOUT). */
+LQS_API int lqs_sv_sync(lqs_sv* sv);
+
+/* ---- gates --------------------------------------------------------------------- */
+
+/* Plain per-gate path: one kernel for one gate, chosen by gate class
+ * (diagonal / permutation / dense one-qubit / dense two-qubit) and by qubit
+ * index (Sec. 2).  wires: n_wires distinct qubits < n (controls first).
+ * params: the gate's parameters (RX..CRY: 1, Rot: 3), or for U2/U4 the
+ * matrix as 8 / 32 doubles (row-major interleaved complex128).
+ * U2/U4 matrices are inspected: a diagonal or anti-diagonal matrix takes the
+ * diagonal or permutation kernels (only nonzero entries are used, Sec. 2). */
+LQS_API int lqs_apply_gate(lqs_sv* sv, int gate, const int* wires, int n_wires, const double* params, int n_params,
+                   int inverse);
+
+/* The "general approach" of Sec. 3.1: apply a dense 2^m x 2^m matrix
+ * (m = n_wires = 1 or 2; row-major interleaved complex128, host) with the
+ * dense kernels and no inspection of its structure. */
+LQS_API int lqs_apply_matrix(lqs_sv* sv, const int* wires, int n_wires, const double* matrix);
+
+/* Fused path: the host planner groups the circuit into segments whose
+ * non-diagonal targets fit one tile of 2^k amplitudes (low contiguous qubits
+ * plus chosen high qubits); each segment is one HBM pass in which the tile is
+ * staged in shared memory by bulk asynchronous copies and all of its gates are
+ * applied on chip.  Gates on disjoint wires may be reordered; the result equals
+ * applying ops[0..n_ops) in order.  params: the circuit's parameter array. */
+LQS_API int lqs_apply_fused(lqs_sv* sv, const lqs_op* ops, int n_ops, const double* params, int n_params,
+                    const lqs_fuse_cfg* cfg_or_null);
+
+/* Host-only view of the fused plan (no GPU work, usable without a device):
+ * *n_segments receives the number of HBM passes; when seg_qubit_mask is
+ * non-null it receives each segment's tile qubit set (capacity `cap`), and
+ * op_segment (n_ops entries, optional) each op's segment.  Ops executed
+ * segment by segment in their original relative order reproduce the circuit. */
+LQS_API int lqs_plan_fused(int n_qubits, int dtype, const lqs_op* ops, int n_ops, const lqs_fuse_cfg* cfg_or_null,
+                   int* n_segments, uint64_t* seg_qubit_mask, int cap, int* op_segment);
+
+/* ---- measurement -------------------------------------------------------------- */
+
+/* <psi|psi> accumulated in float64. */
+LQS_API int lqs_norm2(lqs_sv* sv, double* out_host);
+
+/* Expectation value of H = sum_w coeff_w P_w (Listing 1: qml.expval(H)),
+ * accumulated in float64 with deterministic two-stage reductions (no float
+ * atomics).  *out_host = sum_w coeff_w <P_w>; per_term_host (optional,
+ * n_terms entries) receives each <P_w>.  Synchronous. */
+LQS_API int lqs_expval(lqs_sv* sv, const lqs_pauli* terms, int n_terms, double* out_host, double* per_term_host);
+
+/* ---- gradients --------------------------------------------------------------- */
+
+/* Adjoint-method gradient of E(theta) = <psi(theta)|H|psi(theta)> for every
+ * parameter slot, in one reverse sweep.  psi must hold the state AFTER the
+ * circuit (ops, params) was applied; the sweep computes lambda = H psi and,
+ * for gates l = L..1, g += Im-part inner products of lambda with the gate's
+ * generator applied to psi, then un-applies the gate from both.  On return psi
+ * holds the circuit's input state again (up to rounding).  Two extra state
+ * buffers are used, allocated once per handle and reused.  grads_host has
+ * n_params entries (slots used by several gates receive the sum);
+ * energy_host (optional) receives E.  Synchronous. */
+LQS_API int lqs_adjoint_grad(lqs_sv* psi, const lqs_op* ops, int n_ops, const double* params, int n_params,
+                     const lqs_pauli* terms, int n_terms, double* grads_host, double* energy_host);
+
+/* ---- batches of small circuits ---------------------------------------------- */
+
+/* One circuit of a batch: its own qubit count, gates, parameters and
+ * observable; starts from |0..0>.  grads (host, n_params entries) and
+ * energy are written by lqs_batch_run. */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_ops;
+  const lqs_op* ops;
+  int32_t n_params;
+  const double* params;
+  int32_t n_terms;
+  const lqs_pauli* terms;
+  double* grads;  /* host, n_params entries, or NULL for energy only */
+  double* energy; /* host, 1 entry */
+} lqs_batch_item;
+
+/* Forward + expectation + adjoint gradient of many independent circuits in
+ * one captured CUDA graph / persistent launch on `cuda_stream`; fusion width
+ * and tile shape come from the autotuner.  Synchronous. */
+LQS_API int lqs_batch_run(const lqs_batch_item* items, int n_items, int dtype, void* cuda_stream);
+
+/* ---- misc ------------------------------------------------------------------------ */
+
+/* Message describing the calling thread's most recent error ("" if none). */
+LQS_API const char* lqs_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+LQS_API int lqs_version(void);
+
+/* Default c128 arithmetic for subsequent calls on this process (lqs_arith). */
+LQS_API int lqs_set_arith(int arith);
+
+/* Number of kernels this library has launched since load (for accounting). */
+LQS_API uint64_t lqs_kernel_launches(void);
+
+/* Per-launch profile records (tracing).  Between lqs_profile_start and
+ * lqs_profile_stop every kernel the library launches is bracketed by CUDA
+ * events on its stream; stop synchronises those streams and returns, per
+ * launch, the kernel family, its device time, and the algorithmic HBM bytes
+ * and float64-equivalent flops the launch had to process (what the method
+ * must move and compute, not what the hardware counters report). */
+typedef struct {
+  char kernel[48];
+  float ms;
+  double bytes;
+  double flops;
+} lqs_launch_record;
+LQS_API int lqs_profile_start(void);
+/* Copies up to `cap` records into `out` (may be NULL), the total into *count. */
+LQS_API int lqs_profile_stop(lqs_launch_record* out, int cap, int* count);
+
+/* Host-only check of the double-float conversions used for complex128
+ * arithmetic (no device needed).  For each in[i]: out[2i] = hi + lo of its
+ * double-float split widened exactly, out[2i+1] = the double the store path
+ * rounds the split back to.  LQS_ERR_ARG on NULL pointers or count < 0. */
+LQS_API int lqs_debug_df_roundtrip(const double* in, double* out, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQS_ABI_H_INCLUDED */

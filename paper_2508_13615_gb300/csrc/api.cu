@@ -1,0 +1,421 @@
+// C ABI entry points (include/lqs.h): validation, handles, dispatch.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "arith.cuh"
+#include "lqs_internal.cuh"
+
+namespace lqs {
+
+static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_arith{LQS_ARITH_DF};
+
+int set_error(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? LQS_ERR_OOM : LQS_ERR_CUDA;
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return code;
+}
+
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---- launch profiling --------------------------------------------------------
+struct ProfRec {
+  std::string name;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t st = nullptr;
+  double bytes = 0, flops = 0;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(cudaStream_t s, const char* name, double bytes, double flops) : st(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  ProfRec r;
+  r.name = name;
+  r.st = s;
+  r.bytes = bytes;
+  r.flops = flops;
+  r.e0 = pool_event();
+  r.e1 = pool_event();
+  cudaEventRecord(r.e0, s);
+  idx = (int)g_prof.size();
+  g_prof.push_back(r);
+}
+ProfScope::~ProfScope() {
+  if (idx < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (idx < (int)g_prof.size()) cudaEventRecord(g_prof[idx].e1, g_prof[idx].st);
+}
+
+const char* arith_tag(int dtype, int arith) {
+  if (dtype == LQS_C64) return "f32";
+  return arith == LQS_ARITH_F64 ? "f64" : "df";
+}
+
+double kop_touched_fraction(const KOp& o) {
+  const double c = std::ldexp(1.0, -__builtin_popcountll(o.cmask));
+  return o.kind == K_SWAP ? 0.5 * c : c;
+}
+double kop_flops_per_amp(const KOp& o) {
+  switch (o.kind) {
+    case K_PHASE: return o.special ? 0.0 : 6.0;
+    case K_DIAG1: return 6.0;
+    case K_DIAG2: return 6.0;
+    case K_ANTI1: return o.special == 1 ? 0.0 : 6.0;
+    case K_SWAP: return 0.0;
+    case K_DENSE1: return 14.0;
+    case K_DENSE1R: return 6.0;
+    case K_DENSE2: return 30.0;
+  }
+  return 0.0;
+}
+
+int current_arith(int requested) {
+  if (requested == LQS_ARITH_F64 || requested == LQS_ARITH_DF) return requested;
+  return g_arith.load();
+}
+
+int sv_scratch(SV* sv, int slot, size_t bytes, void** out) {
+  if (slot < 0 || slot > 2) return set_error(LQS_ERR_ARG, "internal: scratch slot");
+  if (sv->scratch_bytes[slot] < bytes) {
+    if (sv->scratch[slot]) {
+      LQS_CUDA_TRY(cudaStreamSynchronize(sv->stream));
+      cudaFree(sv->scratch[slot]);
+      sv->scratch[slot] = nullptr;
+      sv->scratch_bytes[slot] = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(scratch)");
+    sv->scratch[slot] = p;
+    sv->scratch_bytes[slot] = bytes;
+  }
+  *out = sv->scratch[slot];
+  return LQS_OK;
+}
+
+static int check_sv(const lqs_sv* h) {
+  if (!h) return set_error(LQS_ERR_ARG, "state handle is NULL");
+  return LQS_OK;
+}
+
+static SV* S_(lqs_sv* h) { return reinterpret_cast<SV*>(h); }
+static const SV* S_(const lqs_sv* h) { return reinterpret_cast<const SV*>(h); }
+
+__global__ void k_set_basis_f(float2* psi, uint64_t N, uint64_t x) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+    psi[i] = make_float2(i == x ? 1.f : 0.f, 0.f);
+}
+__global__ void k_set_basis_d(double2* psi, uint64_t N, uint64_t x) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+    psi[i] = make_double2(i == x ? 1.0 : 0.0, 0.0);
+}
+
+}  // namespace lqs
+
+using namespace lqs;
+
+extern "C" {
+
+const char* lqs_last_error(void) { return g_err.c_str(); }
+
+int lqs_profile_start(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_prof) {
+    g_event_pool.push_back(r.e0);
+    g_event_pool.push_back(r.e1);
+  }
+  g_prof.clear();
+  g_prof_on = true;
+  return LQS_OK;
+}
+
+int lqs_profile_stop(lqs_launch_record* out, int cap, int* count) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = false;
+  for (auto& r : g_prof) cudaEventSynchronize(r.e1);
+  if (count) *count = (int)g_prof.size();
+  for (int i = 0; out && i < cap && i < (int)g_prof.size(); ++i) {
+    const ProfRec& r = g_prof[i];
+    std::memset(out[i].kernel, 0, sizeof out[i].kernel);
+    std::strncpy(out[i].kernel, r.name.c_str(), sizeof out[i].kernel - 1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    out[i].ms = ms;
+    out[i].bytes = r.bytes;
+    out[i].flops = r.flops;
+  }
+  return LQS_OK;
+}
+
+int lqs_version(void) { return 100; }
+
+uint64_t lqs_kernel_launches(void) { return g_launches.load(); }
+
+int lqs_set_arith(int arith) {
+  if (arith != LQS_ARITH_AUTO && arith != LQS_ARITH_F64 && arith != LQS_ARITH_DF)
+    return set_error(LQS_ERR_ARG, "arith must be LQS_ARITH_AUTO, LQS_ARITH_F64 or LQS_ARITH_DF");
+  g_arith.store(arith == LQS_ARITH_AUTO ? LQS_ARITH_DF : arith);
+  return LQS_OK;
+}
+
+int lqs_sv_alloc(int n_qubits, int dtype, void* device_ptr, void* cuda_stream, lqs_sv** out) {
+  if (!out) return set_error(LQS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > 36) return set_error(LQS_ERR_ARG, "n_qubits must be in [1, 36]");
+  if (dtype != LQS_C64 && dtype != LQS_C128) return set_error(LQS_ERR_ARG, "dtype must be LQS_C64 or LQS_C128");
+  if (device_ptr && (reinterpret_cast<uintptr_t>(device_ptr) & 255u))
+    return set_error(LQS_ERR_ARG, "device_ptr must be 256-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(LQS_ERR_UNSUPPORTED, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  SV* sv = new SV();
+  sv->n = n_qubits;
+  sv->dtype = dtype;
+  sv->stream = static_cast<cudaStream_t>(cuda_stream);
+  sv->device = dev;
+  cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (device_ptr) {
+    sv->d = device_ptr;
+    sv->owns = false;
+  } else {
+    e = cudaMalloc(&sv->d, sv->bytes());
+    if (e != cudaSuccess) {
+      delete sv;
+      return cuda_error(e, "cudaMalloc(state)");
+    }
+    sv->owns = true;
+  }
+  e = cudaMalloc(&sv->d_status, 64);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sv->d_status, 0, 64, sv->stream);
+  if (e != cudaSuccess) {
+    if (sv->owns) cudaFree(sv->d);
+    delete sv;
+    return cuda_error(e, "cudaMalloc(status)");
+  }
+  *out = reinterpret_cast<lqs_sv*>(sv);
+  return LQS_OK;
+}
+
+int lqs_sv_free(lqs_sv* h) {
+  if (!h) return LQS_OK;
+  SV* sv = S_(h);
+  cudaStreamSynchronize(sv->stream);
+  for (int i = 0; i < 3; ++i)
+    if (sv->scratch[i]) cudaFree(sv->scratch[i]);
+  if (sv->d_status) cudaFree(sv->d_status);
+  if (sv->owns && sv->d) cudaFree(sv->d);
+  delete sv;
+  return LQS_OK;
+}
+
+int lqs_sv_info(const lqs_sv* h, void** device_ptr, int* n_qubits, int* dtype) {
+  LQS_TRY(check_sv(h));
+  const SV* sv = S_(h);
+  if (device_ptr) *device_ptr = sv->d;
+  if (n_qubits) *n_qubits = sv->n;
+  if (dtype) *dtype = sv->dtype;
+  return LQS_OK;
+}
+
+int lqs_sv_set_basis(lqs_sv* h, uint64_t x) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  if (x >= sv->N()) return set_error(LQS_ERR_ARG, "basis index >= 2^n");
+  const unsigned grid = (unsigned)std::min<uint64_t>((sv->N() + 255) / 256, (uint64_t)sv->sms * 8);
+  ProfScope ps(sv->stream, "k_set_basis", (double)sv->bytes(), 0.0);
+  if (sv->dtype == LQS_C64) k_set_basis_f<<<grid, 256, 0, sv->stream>>>((float2*)sv->d, sv->N(), x);
+  else k_set_basis_d<<<grid, 256, 0, sv->stream>>>((double2*)sv->d, sv->N(), x);
+  count_launch();
+  LQS_CUDA_TRY(cudaGetLastError());
+  return LQS_OK;
+}
+
+int lqs_sv_copy_from_host(lqs_sv* h, const void* host) {
+  LQS_TRY(check_sv(h));
+  if (!host) return set_error(LQS_ERR_ARG, "host is NULL");
+  SV* sv = S_(h);
+  LQS_CUDA_TRY(cudaMemcpyAsync(sv->d, host, sv->bytes(), cudaMemcpyHostToDevice, sv->stream));
+  return LQS_OK;
+}
+
+int lqs_sv_copy_to_host(const lqs_sv* h, void* host) {
+  LQS_TRY(check_sv(h));
+  if (!host) return set_error(LQS_ERR_ARG, "host is NULL");
+  const SV* sv = S_(h);
+  LQS_CUDA_TRY(cudaMemcpyAsync(host, sv->d, sv->bytes(), cudaMemcpyDeviceToHost, sv->stream));
+  LQS_CUDA_TRY(cudaStreamSynchronize(sv->stream));
+  return LQS_OK;
+}
+
+int lqs_sv_sync(lqs_sv* h) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  LQS_CUDA_TRY(cudaStreamSynchronize(sv->stream));
+  int status[4] = {0, 0, 0, 0};
+  LQS_CUDA_TRY(cudaMemcpy(status, sv->d_status, sizeof status, cudaMemcpyDeviceToHost));
+  if (status[0]) {
+    cudaMemsetAsync(sv->d_status, 0, 64, sv->stream);
+    return set_error(LQS_ERR_TIMEOUT, "a device-side wait gave up (code " + std::to_string(status[0]) + ")");
+  }
+  return LQS_OK;
+}
+
+int lqs_apply_gate(lqs_sv* h, int gate, const int* wires, int n_wires, const double* params, int n_params,
+                   int inverse) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  std::vector<KOp> ops;
+  const double* matrix = nullptr;
+  if (gate == LQS_U2 || gate == LQS_U4) {
+    const int need = gate == LQS_U2 ? 8 : 32;
+    if (!params || n_params < need)
+      return set_error(LQS_ERR_ARG, std::string(gate == LQS_U2 ? "U2" : "U4") + " needs its matrix as " +
+                                        std::to_string(need) + " doubles in params");
+    matrix = params;
+  }
+  LQS_TRY(lower_gate(sv->n, gate, wires, n_wires, params, n_params, matrix, inverse, -1, false, false, ops));
+  const int arith = current_arith(LQS_ARITH_AUTO);
+  for (const KOp& k : ops) LQS_TRY(launch_gate(sv, k, arith));
+  return LQS_OK;
+}
+
+int lqs_apply_matrix(lqs_sv* h, const int* wires, int n_wires, const double* matrix) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  if (n_wires != 1 && n_wires != 2) return set_error(LQS_ERR_ARG, "lqs_apply_matrix takes 1 or 2 wires");
+  std::vector<KOp> ops;
+  LQS_TRY(lower_gate(sv->n, n_wires == 1 ? LQS_U2 : LQS_U4, wires, n_wires, nullptr, 0, matrix, 0, -1, false, true,
+                     ops));
+  const int arith = current_arith(LQS_ARITH_AUTO);
+  for (const KOp& k : ops) LQS_TRY(launch_gate(sv, k, arith));
+  return LQS_OK;
+}
+
+int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* params, int n_params,
+                    const lqs_fuse_cfg* cfg) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  std::vector<KOp> kops;
+  LQS_TRY(lower_ops(sv->n, ops, n_ops, params, n_params, false, kops));
+  PlanCfg pc;
+  int arith = LQS_ARITH_AUTO;
+  LQS_TRY(resolve_cfg(sv->n, sv->dtype, cfg, pc, &arith));
+  std::vector<Segment> segs;
+  LQS_TRY(plan_segments(sv->n, kops, pc, segs));
+  for (const Segment& s : segs) LQS_TRY(launch_segment(sv, kops, s, pc, arith));
+  return LQS_OK;
+}
+
+int lqs_plan_fused(int n_qubits, int dtype, const lqs_op* ops, int n_ops, const lqs_fuse_cfg* cfg,
+                   int* n_segments, uint64_t* seg_qubit_mask, int cap, int* op_segment) {
+  if (n_qubits < 1 || n_qubits > 36) return set_error(LQS_ERR_ARG, "n_qubits must be in [1, 36]");
+  if (dtype != LQS_C64 && dtype != LQS_C128) return set_error(LQS_ERR_ARG, "bad dtype");
+  if (!n_segments) return set_error(LQS_ERR_ARG, "n_segments is NULL");
+  if (n_ops < 0 || (n_ops > 0 && !ops)) return set_error(LQS_ERR_ARG, "bad ops");
+  // The plan depends only on gate classes and wires: lower with zero angles.
+  int np_needed = 0;
+  for (int i = 0; i < n_ops; ++i) np_needed = std::max(np_needed, ops[i].param_idx + 3);
+  std::vector<double> zeros((size_t)std::max(np_needed, 1), 0.0);
+  // Map lowered ops back to the caller's ops: lower one op at a time.
+  std::vector<KOp> kops;
+  std::vector<int> owner;
+  for (int i = 0; i < n_ops; ++i) {
+    const size_t before = kops.size();
+    LQS_TRY(lower_ops(n_qubits, ops + i, 1, zeros.data(), (int)zeros.size(), false, kops));
+    owner.insert(owner.end(), kops.size() - before, i);
+  }
+  PlanCfg pc;
+  int arith = LQS_ARITH_AUTO;
+  LQS_TRY(resolve_cfg(n_qubits, dtype, cfg, pc, &arith));
+  std::vector<Segment> segs;
+  LQS_TRY(plan_segments(n_qubits, kops, pc, segs));
+  *n_segments = (int)segs.size();
+  if (seg_qubit_mask)
+    for (int s = 0; s < (int)segs.size() && s < cap; ++s) seg_qubit_mask[s] = segs[s].qmask;
+  if (op_segment) {
+    for (int i = 0; i < n_ops; ++i) op_segment[i] = -1;
+    for (int s = 0; s < (int)segs.size(); ++s)
+      for (int k : segs[s].ops) op_segment[owner[k]] = s;
+  }
+  return LQS_OK;
+}
+
+int lqs_norm2(lqs_sv* h, double* out_host) {
+  LQS_TRY(check_sv(h));
+  if (!out_host) return set_error(LQS_ERR_ARG, "out_host is NULL");
+  return run_norm2(S_(h), current_arith(LQS_ARITH_AUTO), out_host);
+}
+
+int lqs_expval(lqs_sv* h, const lqs_pauli* terms, int n_terms, double* out_host, double* per_term_host) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  if (!out_host) return set_error(LQS_ERR_ARG, "out_host is NULL");
+  if (n_terms < 0 || (n_terms > 0 && !terms)) return set_error(LQS_ERR_ARG, "bad terms");
+  const uint64_t lim = sv->N() - 1;
+  for (int i = 0; i < n_terms; ++i)
+    if ((terms[i].x_mask | terms[i].z_mask) & ~lim)
+      return set_error(LQS_ERR_ARG, "term " + std::to_string(i) + " acts on a qubit >= n");
+  PlanCfg pc;
+  int arith = LQS_ARITH_AUTO;
+  LQS_TRY(resolve_cfg(sv->n, sv->dtype, nullptr, pc, &arith));
+  return run_expval(sv, terms, n_terms, pc, arith, out_host, per_term_host, nullptr);
+}
+
+int lqs_adjoint_grad(lqs_sv* h, const lqs_op* ops, int n_ops, const double* params, int n_params,
+                     const lqs_pauli* terms, int n_terms, double* grads_host, double* energy_host) {
+  LQS_TRY(check_sv(h));
+  SV* sv = S_(h);
+  if (n_params < 0 || (n_params > 0 && !grads_host)) return set_error(LQS_ERR_ARG, "grads_host is NULL");
+  if (n_terms < 0 || (n_terms > 0 && !terms)) return set_error(LQS_ERR_ARG, "bad terms");
+  const uint64_t lim = sv->N() - 1;
+  for (int i = 0; i < n_terms; ++i)
+    if ((terms[i].x_mask | terms[i].z_mask) & ~lim)
+      return set_error(LQS_ERR_ARG, "term " + std::to_string(i) + " acts on a qubit >= n");
+  std::vector<KOp> kops;
+  LQS_TRY(lower_ops(sv->n, ops, n_ops, params, n_params, true, kops));
+  PlanCfg pc;
+  int arith = LQS_ARITH_AUTO;
+  LQS_TRY(resolve_cfg(sv->n, sv->dtype, nullptr, pc, &arith));
+  return run_adjoint(sv, kops, n_params, terms, n_terms, pc, arith, grads_host, energy_host);
+}
+
+// Host-side check of the double-float conversions (no device needed): for
+// each input x, out[2i] = hi + lo widened exactly, out[2i+1] = the double the
+// store path produces.  Exposed for CPU tests of the bit manipulation.
+int lqs_debug_df_roundtrip(const double* in, double* out, int64_t count) {
+  if (!in || !out || count < 0) return set_error(LQS_ERR_ARG, "bad arguments");
+  for (int64_t i = 0; i < count; ++i) {
+    const DF v = d2df(in[i]);
+    out[2 * i] = (double)v.h + (double)v.l;
+    out[2 * i + 1] = df2d(v);
+  }
+  return LQS_OK;
+}
+
+}  // extern "C"

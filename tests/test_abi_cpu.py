@@ -1,0 +1,100 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, validates arguments on the host, and its double-float
+conversions meet their stated bounds."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2508_13615_gb300 as L
+from paper_2508_13615_gb300 import lqs as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lqs.h")).read()
+    return sorted(set(re.findall(r"LQS_API\s+[\w\s\*]+?\b(lqs_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_core_calls():
+    names = declared_symbols()
+    for core in ("lqs_sv_alloc", "lqs_apply_gate", "lqs_apply_fused", "lqs_expval", "lqs_adjoint_grad"):
+        assert core in names
+    assert len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_binding_has_the_same_names():
+    for n in declared_symbols():
+        assert hasattr(L, n), n
+
+
+def test_version_and_errors():
+    assert L.lqs_version() >= 100
+    with pytest.raises(L.LqsError) as e:
+        L.lqs_set_arith(7)
+    assert e.value.code == B.LQS_ERR_ARG
+    assert "arith" in L.lqs_last_error()
+
+
+def test_alloc_without_device_reports_unsupported():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.LqsError) as e:
+        L.lqs_sv_alloc(4, "c128")
+    assert e.value.code == B.LQS_ERR_UNSUPPORTED
+
+
+class _Op:
+    def __init__(self, name, wires, pidx=-1, matrix=None, inverse=False):
+        self.name, self.wires, self.pidx, self.matrix, self.inverse = name, wires, pidx, matrix, inverse
+
+
+@pytest.mark.parametrize("ops,msg", [
+    ([_Op("CNOT", (1, 1))], "repeated wire"),
+    ([_Op("H", (9,))], "outside"),
+    ([_Op("U2", (0,))], "matrix is NULL"),
+])
+def test_plan_validates_gates_before_any_work(ops, msg):
+    with pytest.raises(L.LqsError) as e:
+        L.lqs_plan_fused(8, "c128", ops)
+    assert e.value.code == B.LQS_ERR_ARG and msg in str(e.value)
+
+
+@pytest.mark.parametrize("cfg", [{"tile_qubits": 20}, {"tile_qubits": 10, "low_qubits": 9}, {"arith": 9}])
+def test_plan_validates_cfg(cfg):
+    with pytest.raises(L.LqsError):
+        L.lqs_plan_fused(20, "c128", [_Op("H", (0,))], cfg)
+
+
+def test_df_split_is_within_two_to_minus_46():
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(size=20000) * 10.0 ** rng.integers(-30, 30, 20000),
+                        [1.0, -1.0, 0.5, 2.0 ** -20, np.pi, -np.e, 2.0 ** -103, 2.0 ** 126]])
+    x = x[(np.abs(x) >= 2.0 ** -103) & (np.abs(x) < 2.0 ** 127)]  # the documented range
+    out = L.lqs_debug_df_roundtrip(x)
+    err = np.abs(out - x[:, None])
+    big = np.abs(x) >= 2.0 ** -80  # the low float is normal: relative bound
+    assert (err[big] / np.abs(x[big])[:, None]).max() <= 2.0 ** -46
+    assert err[~big].max() <= 2.0 ** -125  # subnormal low part flushed: absolute bound
+    # the store path rounds hi + lo to the nearest double: it equals the exact widening sum
+    np.testing.assert_array_equal(out[big, 0], out[big, 1])
+    # exact for doubles with at most 47 significant bits
+    y = np.round(rng.normal(size=1000) * 2 ** 40) / 2 ** 20
+    np.testing.assert_array_equal(L.lqs_debug_df_roundtrip(y)[:, 1], y)
+
+
+def test_df_flushes_tiny_and_keeps_zero():
+    x = np.array([0.0, -0.0, 1e-40, -2.0 ** -104, 2.0 ** -102])
+    out = L.lqs_debug_df_roundtrip(x)[:, 1]
+    np.testing.assert_array_equal(out[:4], 0.0)
+    assert out[4] == 2.0 ** -102

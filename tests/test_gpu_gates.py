@@ -1,0 +1,109 @@
+"""Plain per-gate path on the GPU vs the CPU oracle (element by element)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import MODES, TOL, gpu_state, max_abs, set_mode
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def psi12():
+    return W.gaussian_state(12, 1)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_single_gate_suite_12q(psi12, dtype, arith):
+    """Every X/H/RZ/RY/U2 target and every ordered CNOT/CZ/SWAP pair, each from a
+    fresh copy of the seeded 12-qubit state."""
+    set_mode(arith)
+    worst = 0.0
+    with gpu_state(12, dtype, psi12) as sv:
+        for c in W.single_gate_suite_12q(1):
+            sv.from_numpy(psi12)
+            sv.apply(c, fused=False)
+            got = sv.numpy()
+            want = oracle.run_circuit(c, psi12)
+            err = max_abs(got, want)
+            worst = max(worst, err)
+            assert err <= TOL[dtype], (c.ops[0].name, c.ops[0].wires, err)
+    print(f"worst {dtype}/{arith}: {worst:.3e}")
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_every_gate_every_size(dtype, arith, n):
+    set_mode(arith)
+    psi0 = W.gaussian_state(n, 30 + n)
+    rng = np.random.default_rng(n)
+    with gpu_state(n, dtype, psi0) as sv:
+        for name, m, npar in W.GATES:
+            if m > n:
+                continue
+            for trial in range(4):
+                wires = tuple(int(w) for w in rng.permutation(n)[:m])
+                vals = list(rng.uniform(0, 2 * math.pi, npar))
+                mat = W.haar_unitary(1 << m, int(rng.integers(1 << 30))) if name in ("U2", "U4") else None
+                c = W.Circuit(n).add(name, wires, vals, matrix=mat, inverse=bool(trial & 1) and name not in ("U2", "U4"))
+                sv.from_numpy(psi0)
+                sv.apply(c, fused=False)
+                err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
+                assert err <= TOL[dtype], (name, wires, err)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_structured_user_matrices_take_special_kernels(dtype, arith):
+    """Diagonal / anti-diagonal / phase U2 and diagonal U4 matrices are lowered to
+    the diagonal and permutation classes; results must not change."""
+    set_mode(arith)
+    n = 7
+    psi0 = W.gaussian_state(n, 5)
+    mats = [np.diag([np.exp(0.3j), np.exp(-1.1j)]), np.array([[0, 1j], [np.exp(0.7j), 0]]), np.diag([1, np.exp(0.2j)]),
+            np.diag(np.exp(1j * np.array([0.1, 0.2, 0.3, 0.4])))]
+    with gpu_state(n, dtype, psi0) as sv:
+        for m in mats:
+            name = "U2" if m.shape[0] == 2 else "U4"
+            c = W.Circuit(n).add(name, (5,) if name == "U2" else (6, 2), matrix=m)
+            sv.from_numpy(psi0)
+            sv.apply(c, fused=False)
+            assert max_abs(sv.numpy(), oracle.run_circuit(c, psi0)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_general_matrix_path_equals_dedicated(dtype, arith):
+    """Sec. 3.1's comparison: X and CNOT as dense 2x2 / 4x4 matrices ('general
+    approach') give the same state as the dedicated permutation kernels.  The
+    permutation moves stored bits; the dense kernel computes 0*a + 1*b, exact in
+    float32/float64 and within the 2^-46 double-float split otherwise."""
+    tol = 1e-14 if arith == "df" else 0.0
+    import paper_2508_13615_gb300 as L
+    set_mode(arith)
+    n = 10
+    psi0 = W.gaussian_state(n, 8)
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    CN = np.eye(4, dtype=complex)[[0, 1, 3, 2]]
+    with gpu_state(n, dtype, psi0) as a, gpu_state(n, dtype, psi0) as b:
+        for t in range(n):
+            a.from_numpy(psi0)
+            b.from_numpy(psi0)
+            a.apply_gate("X", (t,))
+            L.lqs_apply_matrix(b.h, (t,), X)
+            assert max_abs(a.numpy(), b.numpy()) <= tol
+            c = (t + 3) % n
+            a.apply_gate("CNOT", (c, t))
+            L.lqs_apply_matrix(b.h, (c, t), CN)
+            assert max_abs(a.numpy(), b.numpy()) <= tol
+
+
+def test_validation_errors_leave_state_untouched():
+    import paper_2508_13615_gb300 as L
+    psi0 = W.gaussian_state(6, 2)
+    with gpu_state(6, "c128", psi0) as sv:
+        for bad in [("CNOT", (2, 2), ()), ("H", (6,), ()), ("RX", (1,), ()), ("U2", (0,), np.eye(3))]:
+            with pytest.raises((L.LqsError, ValueError)):
+                sv.apply_gate(*bad)
+        np.testing.assert_array_equal(sv.numpy(), psi0)
