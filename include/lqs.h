@@ -155,7 +155,7 @@ LQS_API int lqs_sv_sync(lqs_sv* sv);
  * (diagonal / permutation / dense one-qubit / dense two-qubit) and by qubit
  * index (Sec. 2).  wires: n_wires distinct qubits < n (controls first).
  * params: the gate's parameters (RX..CRY: 1, Rot: 3), or for U2/U4 the
- * matrix as 8 / 32 doubles (row-major interleaved complex128).
+ * matrix as exactly 8 / 32 doubles (row-major interleaved complex128).
  * U2/U4 matrices are inspected: a diagonal or anti-diagonal matrix takes the
  * diagonal or permutation kernels (only nonzero entries are used, Sec. 2). */
 LQS_API int lqs_apply_gate(lqs_sv* sv, int gate, const int* wires, int n_wires, const double* params, int n_params,

@@ -294,7 +294,7 @@ int lqs_apply_gate(lqs_sv* h, int gate, const int* wires, int n_wires, const dou
   const double* matrix = nullptr;
   if (gate == LQS_U2 || gate == LQS_U4) {
     const int need = gate == LQS_U2 ? 8 : 32;
-    if (!params || n_params < need)
+    if (!params || n_params != need)
       return set_error(LQS_ERR_ARG, std::string(gate == LQS_U2 ? "U2" : "U4") + " needs its matrix as " +
                                         std::to_string(need) + " doubles in params");
     matrix = params;

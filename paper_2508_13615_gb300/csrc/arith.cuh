@@ -220,6 +220,7 @@ struct ArF32 {
     return make_float2(re, im);
   }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) { return make_float2(c0 * a.x + c1 * b.x, c0 * a.y + c1 * b.y); }
+  static LQS_HD C kmul(C a, C b) { return cmul(a, b); }
   static LQS_HD W neg(W a) { return make_float2(-a.x, -a.y); }
   static LQS_HD W mul_i(W a) { return make_float2(-a.y, a.x); }
   static LQS_HD W add(W a, W b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -258,6 +259,7 @@ struct ArF64 {
     return make_double2(re, im);
   }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) { return make_double2(c0 * a.x + c1 * b.x, c0 * a.y + c1 * b.y); }
+  static LQS_HD C kmul(C a, C b) { return cmul(a, b); }
   static LQS_HD W neg(W a) { return make_double2(dneg(a.x), dneg(a.y)); }
   static LQS_HD W mul_i(W a) { return make_double2(dneg(a.y), a.x); }
   static LQS_HD W add(W a, W b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -317,6 +319,10 @@ struct ArDF {
     DAcc im = df_prod(a.im, c0);
     df_mac(im, b.im, c1);
     return DFC{df_norm(re), df_norm(im)};
+  }
+  static LQS_HD C kmul(C a, C b) {
+    const DFC r = cmul(a, DFC{b.re, b.im});
+    return DFK{r.re, r.im};
   }
   static LQS_HD W neg(W a) { return DFC{df_neg(a.re), df_neg(a.im)}; }
   static LQS_HD W mul_i(W a) { return DFC{df_neg(a.im), a.re}; }

@@ -23,7 +23,7 @@ namespace lqs {
 // ---------------------------------------------------------------------------
 int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* arith) {
   const int kmax = dtype == LQS_C64 ? 14 : 13;  // tile <= 128 KiB of shared memory
-  pc.k = dtype == LQS_C64 ? 13 : 12;
+  pc.k = reg_tile_qubits(dtype);                  // the register-tile kernel's shape
   pc.b = dtype == LQS_C64 ? 5 : 4;
   pc.max_ops = kMaxTileOps;
   int ar = LQS_ARITH_AUTO;
@@ -283,6 +283,19 @@ static int launch_fused_t(SV* sv, const std::vector<KOp>& ops, const Segment& se
 int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith) {
   // A lone gate is cheaper as a plain pass: it only touches the amplitudes it changes.
   if (seg.ops.size() == 1) return launch_gate(sv, ops[seg.ops[0]], arith);
+  const int k = std::min(pc.k, sv->n), b = std::min(pc.b, k);
+  if (k == reg_tile_qubits(sv->dtype)) {
+    const int rc = launch_fused_reg(sv, ops, seg, k, b, arith);
+    if (rc != LQS_ERR_UNSUPPORTED) return rc;
+    // the register program (gates plus layout changes) overflowed: split the
+    // segment in two, keeping the order of its gates
+    Segment lo, hi;
+    lo.qmask = hi.qmask = seg.qmask;
+    lo.ops.assign(seg.ops.begin(), seg.ops.begin() + seg.ops.size() / 2);
+    hi.ops.assign(seg.ops.begin() + seg.ops.size() / 2, seg.ops.end());
+    LQS_TRY(launch_segment(sv, ops, lo, pc, arith));
+    return launch_segment(sv, ops, hi, pc, arith);
+  }
   if (sv->dtype == LQS_C64) return launch_fused_t<ArF32>(sv, ops, seg, pc, arith);
   if (arith == LQS_ARITH_F64) return launch_fused_t<ArF64>(sv, ops, seg, pc, arith);
   return launch_fused_t<ArDF>(sv, ops, seg, pc, arith);

@@ -1,0 +1,564 @@
+// Register-resident tile kernel for fused segments.
+//
+// A tile of 2^k amplitudes (k = r + 8) is spread over 256 threads with
+// R = 2^r amplitudes in each thread's registers.  A "layout" assigns r of the
+// tile's k local qubits to register index bits and the other 8 to thread
+// index bits.  A gate whose non-diagonal targets are register qubits is pure
+// register arithmetic: no shared memory, no barrier, no index math beyond
+// compile-time register indices.  Controls and diagonal factors on any qubit
+// become per-amplitude predicates and selects, since each thread knows the
+// local index of every amplitude it holds.  When the next gates need other
+// qubits in registers, the host planner inserts a layout change, one
+// exchange of the tile through shared memory.
+//
+// Double buffering: while a tile is being computed in registers, the next
+// tile's rows are already streaming into the other shared-memory buffer by
+// bulk asynchronous copies; the result is written through the second buffer
+// and stored by bulk copies.
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <type_traits>
+
+#include "arith.cuh"
+#include "lqs_internal.cuh"
+#include "tile.cuh"
+#include "tile_ops.cuh"
+
+namespace lqs {
+
+template <class A> int add_tile_op(TileProg<A>& P, const KOp& o, int gslot);
+template <class A> void init_prog(TileProg<A>& P, int n, uint64_t Q, int k, int b);
+
+constexpr int kRegThreadBits = 8;
+constexpr int kRegThreads = 1 << kRegThreadBits;
+
+template <int R> struct RLog;
+template <> struct RLog<8> { static constexpr int r = 3; };
+template <> struct RLog<16> { static constexpr int r = 4; };
+
+// Registers per thread per dtype: double-float complex128 keeps 8 amplitudes
+// (32 floats), complex64 16 amplitudes (32 floats).
+template <class A> struct RegR { static constexpr int R = 8; };
+template <> struct RegR<ArF32> { static constexpr int R = 16; };
+
+int reg_tile_qubits(int dtype) { return (dtype == LQS_C64 ? 4 : 3) + kRegThreadBits; }
+
+// ---------------------------------------------------------------------------
+// device side
+// ---------------------------------------------------------------------------
+template <class A, int R, int M, class F>
+__device__ __forceinline__ void for_pairs(F&& f) {
+#pragma unroll
+  for (int e = 0; e < R; ++e)
+    if (!(e & (1 << M))) f(e, e | (1 << M));
+}
+
+template <class A, int R, class F>
+__device__ __forceinline__ void dispatch_pairs(int slot, F&& f) {
+  switch (slot) {
+    case 0: for_pairs<A, R, 0>(f); break;
+    case 1: for_pairs<A, R, 1>(f); break;
+    case 2: for_pairs<A, R, 2>(f); break;
+    default: if constexpr (R >= 16) for_pairs<A, R, 3>(f); break;
+  }
+}
+
+template <class A, int R>
+__device__ __forceinline__ void reg_apply(typename A::W (&v)[R], const TOp& o, const typename A::C* coef,
+                                          uint64_t base, uint32_t jt, const uint32_t (&je)[R]) {
+  using W = typename A::W;
+  using C = typename A::C;
+  if ((base & o.ecmask) != o.ecmask) return;  // a control outside the tile is 0
+  const uint32_t lc = o.lcmask;
+  switch (o.kind) {
+    case K_PHASE: {
+      const C f = coef[o.coef];
+#pragma unroll
+      for (int e = 0; e < R; ++e)
+        if (((jt | je[e]) & lc) == lc) v[e] = phase_apply<A>(f, o.special, v[e]);
+      break;
+    }
+    case K_DIAG1: {
+      const C d0 = coef[o.coef], d1 = coef[o.coef + 1];
+      if (o.l0 >= 0) {
+        const uint32_t tb = 1u << o.l0;
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const uint32_t j = jt | je[e];
+          if ((j & lc) == lc) v[e] = A::cmul((j & tb) ? d1 : d0, v[e]);
+        }
+      } else {
+        const C d = (base & o.e0) ? d1 : d0;
+#pragma unroll
+        for (int e = 0; e < R; ++e)
+          if (((jt | je[e]) & lc) == lc) v[e] = A::cmul(d, v[e]);
+      }
+      break;
+    }
+    case K_DIAG2: {
+#pragma unroll
+      for (int e = 0; e < R; ++e) {
+        const uint32_t j = jt | je[e];
+        if ((j & lc) != lc) continue;
+        const int b0 = o.l0 >= 0 ? (int)((j >> o.l0) & 1u) : ((base & o.e0) ? 1 : 0);
+        const int b1 = o.l1 >= 0 ? (int)((j >> o.l1) & 1u) : ((base & o.e1) ? 1 : 0);
+        v[e] = A::cmul(coef[o.coef + 2 * b0 + b1], v[e]);
+      }
+      break;
+    }
+    case K_ANTI1: {
+      const C f0 = coef[o.coef], f1 = coef[o.coef + 1];
+      const bool plain = o.special == 1;
+      dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+        if (((jt | je[e0]) & lc) != lc) return;
+        const W a = v[e0], b = v[e1];
+        if (plain) {
+          v[e0] = b;
+          v[e1] = a;
+        } else {
+          v[e0] = A::cmul(f0, b);
+          v[e1] = A::cmul(f1, a);
+        }
+      });
+      break;
+    }
+    case K_SWAP: {  // targets at slots 1 (t0) and 0 (t1)
+#pragma unroll
+      for (int e = 0; e < R; e += 4) {
+        if (((jt | je[e]) & lc) != lc) continue;
+        const W a = v[e + 2];
+        v[e + 2] = v[e + 1];
+        v[e + 1] = a;
+      }
+      break;
+    }
+    case K_DENSE1: {
+      const C u00 = coef[o.coef], u01 = coef[o.coef + 1], u10 = coef[o.coef + 2], u11 = coef[o.coef + 3];
+      dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+        if (((jt | je[e0]) & lc) != lc) return;
+        const W a = v[e0], b = v[e1];
+        v[e0] = A::cmac2(u00, a, u01, b);
+        v[e1] = A::cmac2(u10, a, u11, b);
+      });
+      break;
+    }
+    case K_DENSE1R: {
+      const typename A::R u00 = CRe<A>::get(coef[o.coef]), u01 = CRe<A>::get(coef[o.coef + 1]),
+                          u10 = CRe<A>::get(coef[o.coef + 2]), u11 = CRe<A>::get(coef[o.coef + 3]);
+      dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+        if (((jt | je[e0]) & lc) != lc) return;
+        const W a = v[e0], b = v[e1];
+        v[e0] = A::rmac2(u00, a, u01, b);
+        v[e1] = A::rmac2(u10, a, u11, b);
+      });
+      break;
+    }
+    case K_DENSE2: {  // targets at slots 1 (t0, most significant) and 0 (t1)
+#pragma unroll
+      for (int e = 0; e < R; e += 4) {
+        if (((jt | je[e]) & lc) != lc) continue;
+        W x[4] = {v[e], v[e + 1], v[e + 2], v[e + 3]};
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) v[e + rr] = A::cmac4(&coef[o.coef + 4 * rr], x);
+      }
+      break;
+    }
+    case K_DPROD: {
+      // C * prod over factor qubits q set in the amplitude's index of f_q.
+      // e1 = local factor qubits (tile bits), e0 = factor qubits outside the
+      // tile; the pool holds C, then local factors, then outside factors, each
+      // in increasing qubit order.
+      const uint32_t LF = (uint32_t)o.e1;
+      C acc = coef[o.coef];
+      uint32_t regbits = 0;
+#pragma unroll
+      for (int m = 0; m < RLog<R>::r; ++m) regbits |= je[1 << m];
+      // thread-bit factors (the amplitude's thread part is fixed per thread)
+      uint32_t rest = LF & ~regbits;
+      while (rest) {
+        const int q = __ffs(rest) - 1;
+        rest &= rest - 1;
+        if ((jt >> q) & 1u) acc = A::kmul(coef[o.coef + 1 + __popc(LF & ((1u << q) - 1u))], acc);
+      }
+      uint64_t ef = o.e0;
+      int ci = o.coef + 1 + __popc(LF);
+      while (ef) {
+        const int q = __ffsll((long long)ef) - 1;
+        ef &= ef - 1;
+        if ((base >> q) & 1ull) acc = A::kmul(coef[ci], acc);
+        ++ci;
+      }
+      // register-bit factors: a doubling table over this thread's amplitudes
+      C tab[R];
+      tab[0] = acc;
+#pragma unroll
+      for (int e = 1; e < R; ++e) {
+        const int m = 31 - __clz(e);  // highest set bit of e
+        const uint32_t qb = je[1 << m];
+        if (LF & qb) tab[e] = A::kmul(coef[o.coef + 1 + __popc(LF & (qb - 1u))], tab[e ^ (1 << m)]);
+        else tab[e] = tab[e ^ (1 << m)];
+      }
+#pragma unroll
+      for (int e = 0; e < R; ++e)
+        if (((jt | je[e]) & lc) == lc) v[e] = A::cmul(tab[e], v[e]);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Exchange-buffer position of local amplitude j: the bits that select a
+// 16-byte word within a 128-byte shared-memory wavefront are XORed with a fold
+// of the higher bits, so the lanes of a warp hit distinct banks whichever
+// qubits the layout puts on them.
+template <int SZ>
+__device__ __forceinline__ uint32_t swz(uint32_t j) {
+  if constexpr (SZ == 16) return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7u);
+  else return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
+}
+
+// Register/thread layout: nibble i of `packed` is the local qubit of layout
+// slot i; slots 0..r-1 are register bits, slots r..k-1 thread bits.
+template <int R>
+__device__ __forceinline__ void set_layout(uint64_t packed, uint32_t tid, int k, uint32_t& jt, uint32_t (&je)[R]) {
+  constexpr int r = RLog<R>::r;
+  jt = 0;
+#pragma unroll
+  for (int m = 0; m < kRegThreadBits; ++m)
+    if (r + m < k) jt |= ((tid >> m) & 1u) << ((packed >> (4 * (r + m))) & 15u);
+#pragma unroll
+  for (int e = 0; e < R; ++e) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int m = 0; m < r; ++m) x |= (uint32_t)((e >> m) & 1) << ((packed >> (4 * m)) & 15u);
+    je[e] = x;
+  }
+}
+
+template <class A, int R>
+__global__ void __launch_bounds__(kRegThreads) k_fused_reg(typename A::S* __restrict__ psi,
+                                                           const __grid_constant__ TileProg<A> P, int* status) {
+  using S = typename A::S;
+  using W = typename A::W;
+  static_assert(sizeof(S) == sizeof(W), "in-place working format");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const TileGeom& G = P.g;
+  const uint32_t nt = 1u << G.k;
+  S* S0 = reinterpret_cast<S*>(smem_raw);  // incoming tiles (bulk loads)
+  S* S1 = S0 + nt;                         // layout exchanges and outgoing tiles
+  W* X1 = reinterpret_cast<W*>(S1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(S1 + nt);
+  const uint32_t tid = threadIdx.x;
+  W v[R];
+  uint32_t jt, je[R];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint64_t t = blockIdx.x;
+  if (t < G.ntiles && tid < 32) tile_load_issue(G, S0, psi, tile_base(G, t), bar);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (; t < G.ntiles; t += gridDim.x) {
+    const uint64_t base = tile_base(G, t);
+    ok = __syncthreads_and(mbar_wait(bar, phase));
+    phase ^= 1u;
+    if (!ok) break;
+    // op 0 is the first layout: registers <- incoming tile
+    set_layout<R>(P.op[0].ecmask, tid, G.k, jt, je);
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+      const S s = S0[jt | je[e]];
+      v[e] = A::load(s);
+    }
+    __syncthreads();  // the incoming buffer is free: prefetch the next tile into it
+    const uint64_t tn = t + gridDim.x;
+    if (tn < G.ntiles && tid < 32) tile_load_issue(G, S0, psi, tile_base(G, tn), bar);
+    for (int i = 1; i < P.nops; ++i) {
+      const TOp& o = P.op[i];
+      if (o.kind == K_LAYOUT) {
+        __syncthreads();  // readers of the previous exchange are done
+#pragma unroll
+        for (int e = 0; e < R; ++e) X1[swz<sizeof(S)>(jt | je[e])] = v[e];
+        __syncthreads();
+        set_layout<R>(o.ecmask, tid, G.k, jt, je);
+#pragma unroll
+        for (int e = 0; e < R; ++e) v[e] = X1[swz<sizeof(S)>(jt | je[e])];
+      } else {
+        reg_apply<A, R>(v, o, P.coef, base, jt, je);
+      }
+    }
+    __syncthreads();  // exchange readers done before the result overwrites the buffer
+#pragma unroll
+    for (int e = 0; e < R; ++e) S1[jt | je[e]] = A::store(v[e]);
+    fence_proxy_async();
+    __syncthreads();
+    if (tid < 32) tile_store_issue(G, psi, S1, base);
+  }
+  if (tid < 32) bulk_wait0();
+  if (!ok && tid == 0) {
+    flag_timeout(status, 4);
+    mbar_wait(bar, phase ^ 1u);  // the load that did not complete (bounded)
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: layouts
+// ---------------------------------------------------------------------------
+static bool two_target(const KOp& o) { return o.kind == K_SWAP || o.kind == K_DENSE2; }
+
+// A diagonal run merged into one op: C * prod_q f_q^bit_q on amplitudes whose
+// `cond` qubits are all 1.
+struct DGroup {
+  uint64_t cond = 0, wires = 0;
+  std::complex<double> C{1.0, 0.0};
+  std::vector<std::pair<int, std::complex<double>>> f;  // (qubit, factor), merged per qubit
+  std::vector<int> members;                             // lowered-op indices
+  void mul(int q, std::complex<double> fq) {
+    for (auto& x : f)
+      if (x.first == q) {
+        x.second *= fq;
+        return;
+      }
+    f.emplace_back(q, fq);
+  }
+};
+
+// Express a diagonal op as a group term; false for kinds that do not factor.
+// K_DIAG1 (t, d0, d1) = d0 * (d1/d0)^bit_t; K_PHASE (set S, f) = f^bit_q on
+// condition S \ {q}, q = the lowest qubit of S.
+static bool group_term(const KOp& o, uint64_t& cond, int& q, std::complex<double>& fq, std::complex<double>& C) {
+  if (o.kind == K_DIAG1 && o.t0 >= 0) {
+    const std::complex<double> d0(o.m[0], o.m[1]), d1(o.m[2], o.m[3]);
+    if (std::abs(d0) == 0.0) return false;
+    cond = o.cmask;
+    q = o.t0;
+    fq = d1 / d0;
+    C = d0;
+    return true;
+  }
+  if (o.kind == K_PHASE && o.cmask) {
+    q = __builtin_ctzll(o.cmask);
+    cond = o.cmask & ~(1ull << q);
+    fq = std::complex<double>(o.m[0], o.m[1]);
+    C = 1.0;
+    return true;
+  }
+  return false;
+}
+
+// One entry of the emitted sequence: a lowered op, or a merged group.
+struct Ent {
+  int op = -1;
+  int group = -1;
+};
+
+template <class A>
+static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Segment& seg, int r) {
+  const TileGeom& G = P.g;
+  const int k = G.k;
+  auto lp = [&](int q) -> int {
+    if (q < 0) return -1;
+    if (q < G.b) return q;
+    for (int m = 0; m < G.r; ++m)
+      if (G.h[m] == q) return G.b + m;
+    return -1;
+  };
+  // 1. merge diagonal runs.  Diagonal ops commute with each other and with
+  // ops on disjoint wires, so a diagonal op may be delayed until the first
+  // later op that touches one of its wires; ops with the same condition set
+  // are multiplied into one group.
+  std::vector<DGroup> groups;
+  std::vector<int> open;  // indices into groups
+  std::vector<Ent> seq;
+  auto close = [&](size_t oi) {
+    const int g = open[oi];
+    if (groups[g].members.size() == 1) seq.push_back(Ent{groups[g].members[0], -1});
+    else seq.push_back(Ent{-1, g});
+    open.erase(open.begin() + oi);
+  };
+  for (int i : seg.ops) {
+    const KOp& o = ops[i];
+    uint64_t cond;
+    int q;
+    std::complex<double> fq, C;
+    if (o.diagonal() && group_term(o, cond, q, fq, C)) {
+      int g = -1;
+      for (int oi : open)
+        if (groups[oi].cond == cond) g = oi;
+      if (g < 0) {
+        groups.emplace_back();
+        g = (int)groups.size() - 1;
+        groups[g].cond = cond;
+        open.push_back(g);
+      }
+      groups[g].C *= C;
+      groups[g].mul(q, fq);
+      groups[g].wires |= o.wire_mask();
+      groups[g].members.push_back(i);
+      continue;
+    }
+    if (!o.diagonal()) {
+      for (size_t oi = open.size(); oi-- > 0;)
+        if (groups[open[oi]].wires & o.wire_mask()) close(oi);
+    }
+    seq.push_back(Ent{i, -1});
+  }
+  while (!open.empty()) close(open.size() - 1);
+
+  // 2. layouts and emission
+  auto nondiag = [&](const Ent& e) { return e.op >= 0 && !ops[e.op].diagonal(); };
+  auto choose = [&](size_t i) {
+    std::vector<int> slot(r, -1);
+    auto has = [&](int q) { return std::find(slot.begin(), slot.end(), q) != slot.end(); };
+    auto put = [&](int q) {
+      if (q < 0 || has(q)) return;
+      for (int m = r - 1; m >= 0; --m)
+        if (slot[m] < 0) {
+          slot[m] = q;
+          return;
+        }
+    };
+    size_t j = i;
+    while (j < seq.size() && !nondiag(seq[j])) ++j;
+    if (j < seq.size() && two_target(ops[seq[j].op])) {
+      slot[1] = lp(ops[seq[j].op].t0);
+      slot[0] = lp(ops[seq[j].op].t1);
+      ++j;
+    }
+    for (; j < seq.size(); ++j) {
+      if (!nondiag(seq[j])) continue;
+      const KOp& o = ops[seq[j].op];
+      if (two_target(o)) break;  // it will need its own exact placement
+      put(lp(o.t0));
+      if (std::count(slot.begin(), slot.end(), -1) == 0) break;
+    }
+    // fill with the highest unused local qubits, leaving low qubits to the
+    // thread (lane) bits so shared-memory rows stay contiguous
+    for (int q = k - 1; q >= 0 && std::count(slot.begin(), slot.end(), -1); --q) put(q);
+    return slot;
+  };
+  auto pack = [&](const std::vector<int>& slot) {
+    uint64_t p = 0;
+    for (int m = 0; m < r; ++m) p |= (uint64_t)slot[m] << (4 * m);
+    int sl = r;
+    for (int q = 0; q < k; ++q)
+      if (std::find(slot.begin(), slot.end(), q) == slot.end()) p |= (uint64_t)q << (4 * sl++);
+    return p;
+  };
+  auto emit_layout = [&](const std::vector<int>& slot) -> int {
+    if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;  // the caller splits the segment
+    TOp t{};
+    t.kind = K_LAYOUT;
+    t.gslot = -1;
+    t.ecmask = pack(slot);
+    P.op[P.nops++] = t;
+    return LQS_OK;
+  };
+  // Tiles arrive and leave in natural order (rows of contiguous amplitudes),
+  // so the first and last layouts put the lanes on the lowest qubits
+  // (registers on the top r) to read and write shared memory without bank
+  // conflicts; layout changes in between go through the swizzled buffer.
+  std::vector<int> natural(r);
+  for (int m = 0; m < r; ++m) natural[m] = k - r + m;
+  std::vector<int> cur = natural;
+  LQS_TRY(emit_layout(cur));
+  for (size_t i = 0; i < seq.size(); ++i) {
+    if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
+    if (seq[i].group >= 0) {
+      const DGroup& g = groups[seq[i].group];
+      auto f = g.f;
+      std::sort(f.begin(), f.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      TOp t{};
+      t.kind = K_DPROD;
+      t.gslot = -1;
+      t.l0 = t.l1 = -1;
+      t.s0 = t.s1 = -1;
+      for (int q = 0; q < G.n; ++q) {
+        if (!((g.cond >> q) & 1)) continue;
+        const int l = lp(q);
+        if (l >= 0) t.lcmask |= 1u << l;
+        else t.ecmask |= 1ull << q;
+      }
+      const int nc = 1 + (int)f.size();
+      if (P.ncoef + nc > kMaxTileCoef) return LQS_ERR_UNSUPPORTED;
+      t.coef = (int16_t)P.ncoef;
+      P.coef[P.ncoef++] = A::cconst(g.C.real(), g.C.imag());
+      uint64_t lf = 0, ef = 0;
+      for (auto& x : f) {  // local factors first (increasing local position = increasing qubit)
+        const int l = lp(x.first);
+        if (l < 0) continue;
+        lf |= 1ull << l;
+        P.coef[P.ncoef++] = A::cconst(x.second.real(), x.second.imag());
+      }
+      for (auto& x : f) {  // then factors on qubits outside the tile
+        if (lp(x.first) >= 0) continue;
+        ef |= 1ull << x.first;
+        P.coef[P.ncoef++] = A::cconst(x.second.real(), x.second.imag());
+      }
+      t.e1 = lf;
+      t.e0 = ef;
+      P.op[P.nops++] = t;
+      continue;
+    }
+    const KOp& o = ops[seq[i].op];
+    if (!o.diagonal()) {
+      const int a = lp(o.t0), b = lp(o.t1);
+      const bool fits = two_target(o) ? (cur[1] == a && cur[0] == b)
+                                      : std::find(cur.begin(), cur.end(), a) != cur.end();
+      if (!fits) {
+        cur = choose(i);
+        LQS_TRY(emit_layout(cur));
+        if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
+      }
+    }
+    const int rc = add_tile_op(P, o, -1);
+    if (rc != LQS_OK) return LQS_ERR_UNSUPPORTED;
+    TOp& t = P.op[P.nops - 1];
+    if (!o.diagonal()) {
+      t.s0 = (int8_t)(std::find(cur.begin(), cur.end(), lp(o.t0)) - cur.begin());
+      t.s1 = o.t1 >= 0 ? (int8_t)(std::find(cur.begin(), cur.end(), lp(o.t1)) - cur.begin()) : (int8_t)-1;
+    }
+  }
+  if (cur != natural) LQS_TRY(emit_layout(natural));
+  return LQS_OK;
+}
+
+template <class A>
+int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {
+  constexpr int R = RegR<A>::R;
+  const int r = RLog<R>::r;
+  static thread_local TileProg<A> P;
+  init_prog(P, sv->n, seg.qmask, k, b);
+  LQS_TRY(build_reg_prog(P, ops, seg, r));
+  const size_t smem = 2 * ((size_t)sizeof(typename A::S) << k) + 16;
+  static bool attr_done = false;
+  if (!attr_done) {
+    LQS_CUDA_TRY(cudaFuncSetAttribute(k_fused_reg<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_done = true;
+  }
+  int per_sm = 0;
+  LQS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_reg<A, R>, kRegThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const uint64_t grid = std::min<uint64_t>(P.g.ntiles, (uint64_t)std::max(sv->sms, 1) * per_sm);
+  double flops = 0.0;
+  for (int i : seg.ops) flops += kop_touched_fraction(ops[i]) * kop_flops_per_amp(ops[i]);
+  const std::string pname = std::string("k_fused_reg/") + arith_tag(sv->dtype, arith);
+  ProfScope ps(sv->stream, pname.c_str(), 2.0 * (double)sv->bytes(), flops * (double)sv->N());
+  k_fused_reg<A, R><<<(unsigned)grid, kRegThreads, smem, sv->stream>>>(static_cast<typename A::S*>(sv->d), P,
+                                                                       sv->d_status);
+  count_launch();
+  LQS_CUDA_TRY(cudaGetLastError());
+  return LQS_OK;
+}
+
+int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {
+  if (sv->dtype == LQS_C64) return launch_fused_reg_t<ArF32>(sv, ops, seg, k, b, arith);
+  if (arith == LQS_ARITH_F64) return launch_fused_reg_t<ArF64>(sv, ops, seg, k, b, arith);
+  return launch_fused_reg_t<ArDF>(sv, ops, seg, k, b, arith);
+}
+
+}  // namespace lqs

@@ -50,6 +50,8 @@ enum KKind : int {
   K_DENSE1R = 5, // real 2x2 on bit t (H RY CRY)
   K_DENSE2 = 6,  // complex 4x4 on bits (t0 = most significant local bit, t1)
   K_DIAG2 = 7,   // diagonal 4x4 on bits (t0, t1)
+  K_LAYOUT = 8,  // register-tile kernel: move amplitudes to a new register/thread bit layout
+  K_DPROD = 9,   // register-tile kernel: merged diagonal run, C * prod_q f_q^bit_q on amplitudes whose cond bits are 1
 };
 
 // Generators for the adjoint method: a parametrised gate U(theta) with
@@ -135,6 +137,10 @@ struct PlanCfg {
 int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* arith);
 int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::vector<Segment>& segs);
 int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith);
+// Register-resident tile kernel (k = reg_tile_qubits(dtype)); returns
+// LQS_ERR_UNSUPPORTED when the segment's program does not fit (split it).
+int reg_tile_qubits(int dtype);
+int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith);
 
 // ---------------------------------------------------------------------------
 // reductions / expectation values / adjoint

@@ -80,21 +80,27 @@ struct PauliProg {
   PWord w[kPassWords];
 };
 
-// Per-thread double-float partial sums are flushed (warp sum, then float64 per
-// warp) every kFlushTiles tiles: at most 64 terms per chain for 2^11-amplitude
-// tiles, which keeps the double-float rounding below 2^-42 relative.
+// Per-thread double-float partial sums (one per word, in shared memory) are
+// flushed every kFlushTiles tiles: warp sum in double-float, then float64
+// per warp.  A chain holds at most kFlushTiles * (tile amplitudes / threads)
+// = 64 (complex128) or 128 (complex64) terms, which keeps the double-float
+// rounding near 2^-41 relative or better.
 constexpr int kFlushTiles = 8;
+
+template <class S> struct PauliTile { static constexpr int k = 11, ept = 8; };     // complex128: 2^11
+template <> struct PauliTile<float2> { static constexpr int k = 12, ept = 16; };  // complex64: 2^12
 
 // mode bit 1: accumulate <P_w>; bit 2: add c_w P_w psi to lambda; bit 4: lambda starts at zero
 template <class A, int MODE>
 __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __restrict__ psi,
                                                         typename A::S* __restrict__ lam,
                                                         const __grid_constant__ PauliProg P, double* partial,
-                                                        int* status) {
+                                                        int pstride, int* status) {
   using S = typename A::S;
   // working view of a tile: complex128 tiles are converted in place to
   // double-float once per tile; complex64 amplitudes are widened on the fly
   using V = typename std::conditional<sizeof(S) == 16, DFC, float2>::type;
+  constexpr int EPT = PauliTile<S>::ept;  // amplitudes per thread in a full tile
   constexpr bool kExp = MODE & 1, kLam = MODE & 2, kFresh = MODE & 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const TileGeom& G = P.g;
@@ -104,25 +110,21 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
   V* T = reinterpret_cast<V*>(buf);
   V* LT = reinterpret_cast<V*>(lbuf);
   double* wacc = reinterpret_cast<double*>(smem_raw + (size_t)nt * sizeof(S) * (kLam ? 2 : 1));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(wacc + kTileWarps * kPassWords);
+  DAcc* sacc = reinterpret_cast<DAcc*>(wacc + kTileWarps * kPassWords);  // [word][thread]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sacc + kPassWords * kTileThreads);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kTileWarps * kPassWords; i += blockDim.x) wacc[i] = 0.0;
+  for (int w = 0; w < kPassWords; ++w) sacc[w * kTileThreads + threadIdx.x] = DAcc{0.f, 0.f};
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  DAcc acc[kPassWords];
-#pragma unroll
-  for (int w = 0; w < kPassWords; ++w) acc[w] = DAcc{0.f, 0.f};
   auto flush = [&]() {
-#pragma unroll
-    for (int w = 0; w < kPassWords; ++w) {
-      if (w < P.nw) {
-        const DF s = warp_sum(acc[w]);
-        if (lane == 0) wacc[warp * kPassWords + w] += (P.w[w].lowbit >= 0 ? 2.0 : 1.0) * df2d(s);
-        acc[w] = DAcc{0.f, 0.f};
-      }
+    for (int w = 0; w < P.nw; ++w) {
+      const DF s = warp_sum(sacc[w * kTileThreads + threadIdx.x]);
+      if (lane == 0) wacc[warp * kPassWords + w] += (P.w[w].lowbit >= 0 ? 2.0 : 1.0) * df2d(s);
+      sacc[w * kTileThreads + threadIdx.x] = DAcc{0.f, 0.f};
     }
   };
   uint32_t phase = 0;
@@ -151,40 +153,47 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
       __syncthreads();
     }
     if (kExp) {
-      // diagonal words share |psi_j|^2
-      for (uint32_t j = threadIdx.x; j < nt; j += blockDim.x) {
-        const DFC v = to_dfc(T[j]);
-        DAcc pa = df_prod(v.re, v.re);
-        df_mac(pa, v.im, v.im);
-        const DF p = df_norm(pa);
+      // |psi_j|^2 of this thread's amplitudes, shared by every diagonal word
+      DF p[EPT];
 #pragma unroll
-        for (int w = 0; w < kPassWords; ++w) {
-          if (w < P.nw && P.w[w].lowbit < 0) {
-            const bool neg = ((__popcll(base & P.w[w].ze) + __popc(j & P.w[w].zl)) & 1) != 0;
-            df_acc(acc[w], neg ? df_neg(p) : p);
-          }
+      for (int i = 0; i < EPT; ++i) {
+        const uint32_t j = threadIdx.x + i * kTileThreads;
+        p[i] = DF{0.f, 0.f};
+        if (j < nt) {
+          const DFC v = to_dfc(T[j]);
+          DAcc pa = df_prod(v.re, v.re);
+          df_mac(pa, v.im, v.im);
+          p[i] = df_norm(pa);
         }
       }
-      // X/Y words: pairs {j, j^x}; the two orders are conjugates, so one is
-      // counted (doubled at the flush)
+      for (int w = 0; w < P.nw; ++w) {
+        const PWord& Wd = P.w[w];
+        DAcc a = sacc[w * kTileThreads + threadIdx.x];
+        const bool tneg = __popcll(base & Wd.ze) & 1;
+        if (Wd.lowbit < 0) {
 #pragma unroll
-      for (int w = 0; w < kPassWords; ++w) {
-        if (w < P.nw && P.w[w].lowbit >= 0) {
-          const PWord& Wd = P.w[w];
-          const bool tneg = __popcll(base & Wd.ze) & 1;
+          for (int i = 0; i < EPT; ++i) {
+            const uint32_t j = threadIdx.x + i * kTileThreads;
+            const bool neg = tneg ^ (__popc(j & Wd.zl) & 1);
+            df_acc(a, neg ? df_neg(p[i]) : p[i]);
+          }
+        } else {
+          // pairs {j, j^x}; the two orders are conjugates, so one is counted
+          // (doubled at the flush)
           const uint8_t fx[1] = {(uint8_t)Wd.lowbit};
           for (uint32_t g = threadIdx.x; g < nt / 2; g += blockDim.x) {
             const uint32_t j = ins0(g, fx, 1);
-            const DFC b = to_dfc(T[j]), a = to_dfc(T[j ^ Wd.xl]);
+            const DFC b = to_dfc(T[j]), c = to_dfc(T[j ^ Wd.xl]);
             const bool neg = tneg ^ (__popc(j & Wd.zl) & 1);
             switch (Wd.ph) {
-              case 0: acc_re_conj(acc[w], a, b, neg); break;
-              case 1: acc_im_conj(acc[w], a, b, !neg); break;
-              case 2: acc_re_conj(acc[w], a, b, !neg); break;
-              default: acc_im_conj(acc[w], a, b, neg); break;
+              case 0: acc_re_conj(a, c, b, neg); break;
+              case 1: acc_im_conj(a, c, b, !neg); break;
+              case 2: acc_re_conj(a, c, b, !neg); break;
+              default: acc_im_conj(a, c, b, neg); break;
             }
           }
         }
+        sacc[w * kTileThreads + threadIdx.x] = a;
       }
       if (++since_flush == kFlushTiles) {
         flush();
@@ -236,8 +245,69 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
     for (int w = threadIdx.x; w < P.nw; w += blockDim.x) {
       double s = 0.0;
       for (int q = 0; q < kTileWarps; ++q) s += wacc[q * kPassWords + w];
-      partial[(size_t)w * gridDim.x + blockIdx.x] = s;
+      partial[(size_t)w * pstride + blockIdx.x] = s;
     }
+}
+
+// One Pauli word whose X/Y qubits do not fit a tile: a global pair pass over
+// (j, j^x) with j's lowest X bit clear.  Expectation partials per block
+// (deterministic), and optionally lambda += c P psi for both members of the
+// pair (each pair belongs to exactly one thread, so there are no races).
+template <class A, bool kLam>
+__global__ void __launch_bounds__(256) k_pauli_wide(const typename A::S* __restrict__ psi,
+                                                    typename A::S* __restrict__ lam, uint64_t npairs, int lowbit,
+                                                    uint64_t x, uint64_t z, int ph, DF c, double* partial) {
+  using S = typename A::S;
+  __shared__ double red[256];
+  DAcc acc{0.f, 0.f};
+  double dacc = 0.0;
+  int cnt = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < npairs; g += stride) {
+    const uint64_t j = ((g >> lowbit) << (lowbit + 1)) | (g & ((1ull << lowbit) - 1));
+    const uint64_t jp = j ^ x;
+    const DFC b = to_dfc(A::load(psi[j])), a = to_dfc(A::load(psi[jp]));
+    const bool neg = __popcll(j & z) & 1;
+    switch (ph) {
+      case 0: acc_re_conj(acc, a, b, neg); break;
+      case 1: acc_im_conj(acc, a, b, !neg); break;
+      case 2: acc_re_conj(acc, a, b, !neg); break;
+      default: acc_im_conj(acc, a, b, neg); break;
+    }
+    if (++cnt == 64) {
+      dacc += df2d(df_norm(acc));
+      acc = DAcc{0.f, 0.f};
+      cnt = 0;
+    }
+    if (kLam) {
+      // lambda_jp += c i^ph (-1)^popc(j&z) psi_j ; lambda_j += c i^ph (-1)^popc(jp&z) psi_jp
+      const uint64_t dst[2] = {jp, j};
+      const DFC src[2] = {b, a};
+      const bool sg[2] = {neg, (__popcll(jp & z) & 1) != 0};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const DFC l0 = to_dfc(A::load(lam[dst[q]]));
+        DAcc re{l0.re.h, l0.re.l}, im{l0.im.h, l0.im.l};
+        DF vr = src[q].re, vi = src[q].im;
+        if (ph & 1) { const DF t_ = vr; vr = df_neg(vi); vi = t_; }
+        if (ph & 2) { vr = df_neg(vr); vi = df_neg(vi); }
+        if (sg[q]) { vr = df_neg(vr); vi = df_neg(vi); }
+        df_mac(re, vr, c);
+        df_mac(im, vi, c);
+        const DFC out{df_norm(re), df_norm(im)};
+        if constexpr (sizeof(S) == 16) lam[dst[q]] = make_double2(df2d(out.re), df2d(out.im));
+        else lam[dst[q]] = make_float2(out.re.h + out.re.l, out.im.h + out.im.l);
+      }
+    }
+  }
+  dacc += df2d(df_norm(acc));
+  red[threadIdx.x] = 2.0 * dacc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
 // out[i] = sum_b partial[i * nb + b], in a fixed order (one block per slot).
@@ -256,15 +326,23 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 }
 
 // Group words into passes: X masks must fit a tile of k qubits (low b qubits
-// plus chosen high qubits); at most kPassWords words per pass.
+// plus chosen high qubits); at most kPassWords words per pass.  Words whose
+// X/Y qubits cannot fit any tile go to `wide` (global pair passes).
 struct PassPlan {
   uint64_t Q;
   std::vector<int> words;
 };
-static int plan_passes(int n, const lqs_pauli* terms, int n_terms, int k, int b, std::vector<PassPlan>& out) {
+static int plan_passes(int n, const lqs_pauli* terms, int n_terms, int k, int b, std::vector<PassPlan>& out,
+                       std::vector<int>& wide) {
   std::vector<char> done(n_terms, 0);
   int left = n_terms;
   const uint64_t low = (b >= 64) ? ~0ull : ((1ull << b) - 1);
+  for (int i = 0; i < n_terms; ++i)
+    if (__builtin_popcountll(terms[i].x_mask | low) > k) {
+      wide.push_back(i);
+      done[i] = 1;
+      --left;
+    }
   while (left) {
     PassPlan p;
     p.Q = low;
@@ -278,7 +356,7 @@ static int plan_passes(int n, const lqs_pauli* terms, int n_terms, int k, int b,
         --left;
       }
     }
-    if (p.words.empty()) return set_error(LQS_ERR_UNSUPPORTED, "a Pauli word has more X/Y qubits than fit a tile");
+    if (p.words.empty()) return set_error(LQS_ERR_ARG, "internal: Pauli pass planner made no progress");
     for (int q = b; q < n && __builtin_popcountll(p.Q) < k; ++q) p.Q |= 1ull << q;
     out.push_back(std::move(p));
   }
@@ -306,13 +384,18 @@ static int lpos(const TileGeom& G, int q) {
 // Tile size for measurement passes: smaller than the fused default so that
 // two tiles (psi and lambda) plus accumulators leave room for 2-3 CTAs per SM.
 static void measure_kb(int n, int dtype, int& k, int& b) {
-  k = dtype == LQS_C64 ? 12 : 11;
+  k = dtype == LQS_C64 ? PauliTile<float2>::k : PauliTile<double2>::k;
   b = dtype == LQS_C64 ? 5 : 4;
   if (n <= k) { k = n; b = n; }
 }
 
+static size_t pauli_smem(size_t amp, int k, bool lam) {
+  return (amp << k) * (lam ? 2 : 1) + sizeof(double) * kTileWarps * kPassWords +
+         sizeof(DAcc) * kPassWords * kTileThreads + 16;
+}
+
 template <class A, int MODE>
-static int launch_pauli(SV* sv, const PauliProg& P, void* lam, double* partial, int grid) {
+static int launch_pauli(SV* sv, const PauliProg& P, void* lam, double* partial, int grid, int pstride) {
   const size_t amp = sizeof(typename A::S);
   // bytes: psi read, plus lambda written (and read unless fresh); flops: 8 per
   // amplitude per word (an amplitude pair product and accumulation)
@@ -320,7 +403,7 @@ static int launch_pauli(SV* sv, const PauliProg& P, void* lam, double* partial, 
   const double bytes = S * (1.0 + ((MODE & 2) ? ((MODE & 4) ? 1.0 : 2.0) : 0.0));
   const std::string pname = std::string((MODE & 2) ? "k_pauli_lambda/" : "k_pauli/") + arith_tag(sv->dtype, std::is_same<A, ArF64>::value ? LQS_ARITH_F64 : LQS_ARITH_DF);
   ProfScope ps(sv->stream, pname.c_str(), bytes, 8.0 * P.nw * (double)sv->N());
-  const size_t smem = (amp << P.g.k) * ((MODE & 2) ? 2 : 1) + sizeof(double) * kTileWarps * kPassWords + 16;
+  const size_t smem = pauli_smem(amp, P.g.k, (MODE & 2) != 0);
   static bool attr = false;
   if (!attr) {
     LQS_CUDA_TRY(cudaFuncSetAttribute(k_pauli<A, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -328,7 +411,7 @@ static int launch_pauli(SV* sv, const PauliProg& P, void* lam, double* partial, 
   }
   k_pauli<A, MODE><<<grid, kTileThreads, smem, sv->stream>>>(static_cast<const typename A::S*>(sv->d),
                                                               static_cast<typename A::S*>(lam), P, partial,
-                                                              sv->d_status);
+                                                              pstride, sv->d_status);
   count_launch();
   LQS_CUDA_TRY(cudaGetLastError());
   return LQS_OK;
@@ -348,22 +431,33 @@ static int pauli_passes(SV* sv, const lqs_pauli* terms, int n_terms, void* lam, 
   int k, b;
   measure_kb(sv->n, sv->dtype, k, b);
   std::vector<PassPlan> passes;
-  LQS_TRY(plan_passes(sv->n, terms, n_terms, k, b, passes));
-  if (passes.empty()) {
+  std::vector<int> wide;
+  LQS_TRY(plan_passes(sv->n, terms, n_terms, k, b, passes, wide));
+  if (passes.empty() && wide.empty()) {
     for (int i = 0; i < n_terms; ++i) vals[i] = 0.0;
+    if (lam) LQS_CUDA_TRY(cudaMemsetAsync(lam, 0, sv->bytes(), sv->stream));
     return LQS_OK;
   }
+  // wide words accumulate into lambda, so it must start at zero
+  const bool lam_zeroed = lam && !wide.empty();
+  if (lam_zeroed) LQS_CUDA_TRY(cudaMemsetAsync(lam, 0, sv->bytes(), sv->stream));
   // partial sums: one slot per word per block, laid out pass by pass
   const uint64_t ntiles = 1ull << (sv->n - k);
   const size_t amp = sizeof(typename A::S);
-  const size_t smem2 = (amp << k) * 2 + sizeof(double) * kTileWarps * kPassWords + 16;
+  const size_t smem2 = pauli_smem(amp, k, true);
   const int grid = occupancy_grid<A>(sv, (const void*)k_pauli<A, 3>, smem2, ntiles);
+  const int wgrid = (int)std::min<uint64_t>(std::max<uint64_t>(sv->N() / 2 / 256, 1), (uint64_t)std::max(sv->sms, 1) * 8);
   size_t slots = 0;
   for (auto& p : passes) slots += p.words.size();
+  const size_t tiled_slots = slots;
+  slots += wide.size();
   void* scratch = nullptr;
-  LQS_TRY(sv_scratch(sv, 2, sizeof(double) * (slots * grid + slots), &scratch));
+  const int pgrid = wide.empty() ? grid : std::max(grid, wgrid);  // partial rows are pgrid wide
+  LQS_TRY(sv_scratch(sv, 2, sizeof(double) * (slots * pgrid + slots), &scratch));
   double* partial = static_cast<double*>(scratch);
-  double* sums = partial + slots * grid;
+  double* sums = partial + slots * pgrid;
+  if (pgrid != grid || pgrid != wgrid)
+    LQS_CUDA_TRY(cudaMemsetAsync(partial, 0, sizeof(double) * slots * pgrid, sv->stream));
   size_t off = 0;
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const PassPlan& pp = passes[pi];
@@ -391,13 +485,34 @@ static int pauli_passes(SV* sv, const lqs_pauli* terms, int n_terms, void* lam, 
       W.ph = (uint32_t)(__builtin_popcountll(t.x_mask & t.z_mask) & 3);
       W.c = split_const(t.coeff);
     }
-    double* part = partial + off * grid;
-    if (!lam) LQS_TRY((launch_pauli<A, 1>(sv, P, nullptr, part, grid)));
-    else if (pi == 0) LQS_TRY((launch_pauli<A, 7>(sv, P, lam, part, grid)));
-    else LQS_TRY((launch_pauli<A, 3>(sv, P, lam, part, grid)));
+    // each word's partial row is pgrid wide; a tiled pass writes `grid` of it
+    double* part = partial + off * pgrid;
+    if (!lam) LQS_TRY((launch_pauli<A, 1>(sv, P, nullptr, part, grid, pgrid)));
+    else if (pi == 0 && !lam_zeroed) LQS_TRY((launch_pauli<A, 7>(sv, P, lam, part, grid, pgrid)));
+    else LQS_TRY((launch_pauli<A, 3>(sv, P, lam, part, grid, pgrid)));
     off += pp.words.size();
   }
-  k_sum_partials<<<(unsigned)slots, 256, 0, sv->stream>>>(partial, grid, sums);
+  for (size_t i = 0; i < wide.size(); ++i) {
+    const lqs_pauli& t = terms[wide[i]];
+    int lowbit = 0;
+    while (!((t.x_mask >> lowbit) & 1)) ++lowbit;
+    const int ph = __builtin_popcountll(t.x_mask & t.z_mask) & 3;
+    double* pw = partial + (tiled_slots + i) * pgrid;
+    const std::string pname = std::string(lam ? "k_pauli_wide_lambda/" : "k_pauli_wide/") +
+                              arith_tag(sv->dtype, std::is_same<A, ArF64>::value ? LQS_ARITH_F64 : LQS_ARITH_DF);
+    ProfScope ps(sv->stream, pname.c_str(), (double)sv->bytes() * (lam ? 3.0 : 1.0), 8.0 * (double)sv->N());
+    if (lam)
+      k_pauli_wide<A, true><<<wgrid, 256, 0, sv->stream>>>(static_cast<const typename A::S*>(sv->d),
+                                                            static_cast<typename A::S*>(lam), sv->N() / 2, lowbit,
+                                                            t.x_mask, t.z_mask, ph, split_const(t.coeff), pw);
+    else
+      k_pauli_wide<A, false><<<wgrid, 256, 0, sv->stream>>>(static_cast<const typename A::S*>(sv->d), nullptr,
+                                                             sv->N() / 2, lowbit, t.x_mask, t.z_mask, ph,
+                                                             split_const(t.coeff), pw);
+    count_launch();
+    LQS_CUDA_TRY(cudaGetLastError());
+  }
+  k_sum_partials<<<(unsigned)slots, 256, 0, sv->stream>>>(partial, pgrid, sums);
   count_launch();
   LQS_CUDA_TRY(cudaGetLastError());
   std::vector<double> h(slots);
@@ -406,6 +521,7 @@ static int pauli_passes(SV* sv, const lqs_pauli* terms, int n_terms, void* lam, 
   off = 0;
   for (auto& p : passes)
     for (int w : p.words) vals[w] = h[off++];
+  for (int w : wide) vals[w] = h[off++];
   int status[2] = {0, 0};
   LQS_CUDA_TRY(cudaMemcpy(status, sv->d_status, sizeof status, cudaMemcpyDeviceToHost));
   if (status[0]) {

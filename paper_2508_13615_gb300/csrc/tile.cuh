@@ -41,7 +41,8 @@ struct TOp {
   uint64_t ecmask;         // controls outside the tile: the op applies on tiles where all are 1
   uint64_t e0, e1;         // diagonal ops: target bits outside the tile
   int16_t gslot;           // adjoint: gradient slot (-1 none)
-  int16_t pad[3];
+  int8_t s0, s1;           // register-tile kernel: register slots of the targets
+  int16_t pad[2];
 };
 
 template <class A>
