@@ -98,6 +98,7 @@ def _load():
         "lqs_set_arith": (i32, [i32]),
         "lqs_kernel_launches": (u64, []),
         "lqs_debug_df_roundtrip": (i32, [dp, dp, i64]),
+        "lqs_expval_static": (i32, [vp, i32, i32, vp, ctypes.POINTER(lqs_pauli), i32, dp, dp]),
         "lqs_profile_start": (i32, []),
         "lqs_profile_stop": (i32, [ctypes.POINTER(lqs_launch_record), i32, ip]),
     }
@@ -372,3 +373,13 @@ def lqs_profile_stop():
     recs = (lqs_launch_record * max(cnt.value, 1))()
     _check(_L.lqs_profile_stop(recs, cnt.value, ctypes.byref(cnt)))
     return [(r.kernel.decode(), float(r.ms), float(r.bytes), float(r.flops)) for r in recs[: cnt.value]]
+
+
+def lqs_expval_static(psi_device_ptr: int, n_qubits: int, dtype, terms, cuda_stream: Optional[int] = None):
+    """Allocation-free <psi|H|psi> over a raw device pointer (see include/lqs.h)."""
+    pa = terms if isinstance(terms, PauliArray) else PauliArray(terms)
+    out = ctypes.c_double()
+    per = np.zeros(max(pa.n, 1), dtype=np.float64)
+    _check(_L.lqs_expval_static(ctypes.c_void_p(psi_device_ptr), int(n_qubits), _dtype_code(dtype), cuda_stream,
+                                pa.ptr(), pa.n, ctypes.byref(out), _dptr(per)))
+    return out.value, per[: pa.n]
