@@ -163,8 +163,21 @@ class Workload:
         self.p2p3()
 
 
-def roofline(records, pk):
-    """Dominant kernel family (by device time) and its achieved fraction."""
+# Peaks derived from the unit counts and clocks of the part (152 SMs, 128 FP32
+# lanes per SM, 2.07 GHz maximum SM clock): 40.3 T FP32 instructions/s.  The
+# double-float complex128 gate math costs about 6.3 FP32 instructions per
+# float64-equivalent flop (a real 2x2 or a complex scale: 38 instructions for
+# 6 flops per amplitude), so its arithmetic peak is 40.3 / 6.3 = 6.4 TFLOP/s
+# float64-equivalent; native complex64 math is 2 flops per FMA lane-cycle.
+FP32_INSTR_PEAK = 152 * 128 * 2.07e9
+DF_INSTR_PER_FLOP = 38.0 / 6.0
+ALU_PEAK_TFLOPS = {"df": FP32_INSTR_PEAK / DF_INSTR_PER_FLOP / 1e12, "f32": 2 * FP32_INSTR_PEAK / 1e12,
+                   "f64": 1.25}
+
+
+def roofline(records, pk, traffic=None):
+    """Dominant kernel family (by device time) and its achieved fraction of the
+    binding roof: HBM bandwidth or the arithmetic rate of its precision."""
     fam = {}
     for name, ms, b, f in records:
         d = fam.setdefault(name, [0, 0.0, 0.0, 0.0])
@@ -176,13 +189,24 @@ def roofline(records, pk):
     name, (cnt, ms, b, f) = max(fam.items(), key=lambda kv: kv[1][1])
     hbm = float(pk.get("hbm_gbs", 6800.0))
     gbs = b / (ms * 1e-3) / 1e9
-    # float64-equivalent arithmetic the double-float kernels deliver, against
-    # GB300's float64 pipe (1.25 TFLOP/s nominal): the alternative bound
     tfl = f / (ms * 1e-3) / 1e12
-    out = {"kernel": name, "launches": cnt, "share": ms / total, "bound": "hbm", "achieved": gbs, "peak": hbm,
-           "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
-           "bytes_per_launch": b / cnt, "ms_per_launch": ms / cnt, "f64eq_tflops": tfl}
+    arith = name.split("/")[-1] if "/" in name else "f32"
+    alu_peak = ALU_PEAK_TFLOPS.get(arith, ALU_PEAK_TFLOPS["f32"])
+    hbm_frac, alu_frac = gbs / hbm, tfl / alu_peak
+    if alu_frac > hbm_frac:
+        out = {"kernel": name, "bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": alu_frac,
+               "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / {DF_INSTR_PER_FLOP:.2f} FP32 "
+                              f"instructions per float64-equivalent flop (double-float)" if arith == "df" else
+                              "derived from unit counts and clocks",
+               "hbm_frac_of_measured": hbm_frac}
+    else:
+        out = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
+               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in pk else
+                              "fallback 6.8 TB/s",
+               "alu_frac": alu_frac}
+    out.update({"traffic": traffic, "launches": cnt, "share": ms / total, "bytes_per_launch": b / cnt,
+                "ms_per_launch": ms / cnt, "f64eq_tflops": tfl, "algorithmic_gbps": gbs})
     fams = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total, 4),
                 "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None} for k, v in fam.items()}
     return out, fams
@@ -249,6 +273,196 @@ def run_reference(args):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# secondary configurations (one JSON line each; not the driver's default run)
+# ---------------------------------------------------------------------------
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def config_adjoint24(args):
+    """24 qubits, 8-layer ansatz (384 parameters), TFIM: adjoint gradient time
+    over forward time (fused forward + expectation), complex128 and complex64,
+    and central differences (h = 1e-6) on a sample of parameters (complex128)."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    n = 24
+    c = W.ansatz(n, 8, 6)
+    terms = W.tfim(n)
+    ops = L.OpArray(c.ops)
+    pa = L.PauliArray(terms)
+    out = {"config": "adjoint24", "metric": "adjoint/forward time", "n_qubits": n, "params": c.n_params}
+    for dtype in ("c128", "c64"):
+        sv = L.StateVector(n, dtype)
+        st = torch.cuda.current_stream()
+
+        def fwd():
+            L.lqs_sv_set_basis(sv.h, 0)
+            L.lqs_apply_fused(sv.h, ops, c.params, None)
+            return L.lqs_expval(sv.h, pa)[0]
+
+        for _ in range(args.warmup):
+            fwd()
+            L.lqs_adjoint_grad(sv.h, ops, c.params, pa)
+        tf, ta = [], []
+        for _ in range(max(args.steps, 3)):
+            e0, e1 = _events()
+            e0.record(st)
+            fwd()
+            e1.record(st)
+            torch.cuda.synchronize()
+            tf.append(e0.elapsed_time(e1))
+            e0.record(st)
+            g, e = L.lqs_adjoint_grad(sv.h, ops, c.params, pa)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ta.append(e0.elapsed_time(e1))
+        rec = {"forward_ms": statistics.median(tf), "adjoint_ms": statistics.median(ta),
+               "adjoint_over_forward": statistics.median(ta) / statistics.median(tf), "energy": e}
+        if dtype == "c128":
+            h = 1e-6
+            fd = []
+            for k in (0, 7, 100, 383):
+                vals = []
+                for sgn in (1, -1):
+                    p = c.params.copy()
+                    p[k] += sgn * h
+                    L.lqs_sv_set_basis(sv.h, 0)
+                    L.lqs_apply_fused(sv.h, ops, p, None)
+                    vals.append(L.lqs_expval(sv.h, pa)[0])
+                fd.append(abs((vals[0] - vals[1]) / (2 * h) - g[k]))
+            rec["max_abs_adjoint_minus_fd"] = max(fd)
+            g128 = g
+        else:
+            rec["max_abs_grad_c64_minus_c128"] = float(np.max(np.abs(g - g128)))
+        out[dtype] = rec
+        sv.close()
+    print(json.dumps(out), flush=True)
+
+
+def config_precision32(args):
+    """32 qubits, 20-layer ansatz: complex64 (32 GiB) vs complex128 (64 GiB) on the
+    fused path; <sum Z_i Z_i+1> in float64 for both, and the complex64 state's
+    relative L2 distance from the complex128 one."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    n = args.n if args.n != N_QUBITS else 32
+    c = W.ansatz(n, 20, 5)
+    terms = W.zz_chain(n)
+    ops = L.OpArray(c.ops)
+    res = {"config": "precision32", "n_qubits": n, "layers": 20, "gates": len(c.ops)}
+    svs = {}
+    for dtype in ("c128", "c64"):
+        sv = L.StateVector(n, dtype)
+        st = torch.cuda.current_stream()
+        e0, e1 = _events()
+        e0.record(st)
+        L.lqs_sv_set_basis(sv.h, 0)
+        L.lqs_apply_fused(sv.h, ops, c.params, None)
+        e1.record(st)
+        torch.cuda.synchronize()
+        e, _ = L.lqs_expval(sv.h, terms)
+        res[dtype] = {"forward_ms": e0.elapsed_time(e1), "energy_zz": e,
+                      "passes": L.lqs_plan_fused(n, dtype, c.ops)[0]}
+        svs[dtype] = sv
+    d2, nb = L.lqs_sv_distance(svs["c64"].h, svs["c128"].h)
+    res["abs_energy_c64_minus_c128"] = abs(res["c64"]["energy_zz"] - res["c128"]["energy_zz"])
+    res["rel_l2_c64_vs_c128"] = math.sqrt(d2 / nb)
+    for sv in svs.values():
+        sv.close()
+    print(json.dumps(res), flush=True)
+
+
+def config_batch256(args):
+    """256 circuits, n ~ U{10..20}, 4..12 ansatz layers, TFIM, complex64: one
+    persistent launch (forward + energy + adjoint gradients) against a loop
+    that runs the circuits one at a time through the same library."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    circs = W.batch_circuits(256, 7)
+    terms = [W.tfim(c.n_qubits) for c in circs]
+    for _ in range(2):
+        e, g = L.lqs_batch_run(circs, terms, "c64")
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(max(args.steps, 3)):
+        t0 = time.perf_counter()
+        e, g = L.lqs_batch_run(circs, terms, "c64")
+        tb.append(time.perf_counter() - t0)
+
+    # the loop baseline: same library, one circuit at a time, with its
+    # arguments marshalled once and one state per qubit count reused
+    ops = [L.OpArray(c.ops) for c in circs]
+    pas = [L.PauliArray(t) for t in terms]
+    svs = {n: L.StateVector(n, "c64") for n in sorted({c.n_qubits for c in circs})}
+
+    def loop():
+        es, gs = [], []
+        for c, oa, pa in zip(circs, ops, pas):
+            h = svs[c.n_qubits].h
+            L.lqs_sv_set_basis(h, 0)
+            L.lqs_apply_fused(h, oa, c.params, None)
+            gg, ee = L.lqs_adjoint_grad(h, oa, c.params, pa)
+            es.append(ee)
+            gs.append(gg)
+        return es, gs
+
+    loop()
+    torch.cuda.synchronize()
+    tl = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        el, gl = loop()
+        tl.append(time.perf_counter() - t0)
+    err_e = max(abs(a - b) for a, b in zip(e, el))
+    err_g = max(float(np.max(np.abs(a - b))) if len(a) else 0.0 for a, b in zip(g, gl))
+    print(json.dumps({"config": "batch256", "circuits": len(circs), "dtype": "c64",
+                      "gates": sum(len(c.ops) for c in circs), "params": sum(c.n_params for c in circs),
+                      "batched_s": statistics.median(tb), "loop_s": statistics.median(tl),
+                      "speedup": statistics.median(tl) / statistics.median(tb),
+                      "max_abs_energy_batched_minus_loop": err_e, "max_abs_grad_batched_minus_loop": err_g}),
+          flush=True)
+
+
+def config_sweep30(args):
+    """Dedicated vs general kernels over every target at 30 qubits complex128
+    (Sec. 3.1, Fig. 3c / 4c on one GPU): X by the permutation kernel against X as
+    a dense 2x2; CNOT(24, t) by the permutation kernel against a dense 4x4."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    n = args.n
+    sv = L.StateVector(n, "c128")
+    L.lqs_sv_set_basis(sv.h, 0)
+    st = torch.cuda.current_stream()
+    Xm = np.array([[0, 1], [1, 0]], dtype=complex)
+    CN = np.eye(4, dtype=complex)[[0, 1, 3, 2]]
+
+    def t_of(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = _events()
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    rows = []
+    S = (1 << n) * 16
+    for t in range(n):
+        c = 24 if t != 24 else 0
+        rows.append({"t": t,
+                     "x_dedicated_ms": t_of(lambda: L.lqs_apply_gate(sv.h, "X", (t,))),
+                     "x_general_ms": t_of(lambda: L.lqs_apply_matrix(sv.h, (t,), Xm)),
+                     "cnot_dedicated_ms": t_of(lambda: L.lqs_apply_gate(sv.h, "CNOT", (c, t))),
+                     "cnot_general_ms": t_of(lambda: L.lqs_apply_matrix(sv.h, (c, t), CN))})
+    sv.close()
+    print(json.dumps({"config": "sweep30", "n_qubits": n, "state_bytes": S, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,11 +472,19 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--config", default="main", choices=["main", "adjoint24", "precision32", "batch256", "sweep30"],
+                    help="secondary measurements (one JSON line each); the default is the headline run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config != "main":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        {"adjoint24": config_adjoint24, "precision32": config_precision32, "batch256": config_batch256,
+         "sweep30": config_sweep30}[args.config](args)
         return
 
     import torch

@@ -188,6 +188,13 @@ LQS_API int lqs_plan_fused(int n_qubits, int dtype, const lqs_op* ops, int n_ops
 /* <psi|psi> accumulated in float64. */
 LQS_API int lqs_norm2(lqs_sv* sv, double* out_host);
 
+/* Distance between two states of the same qubit count (any dtypes):
+ * *diff2 = sum_i |a_i - b_i|^2 and *norm2_b = sum_i |b_i|^2, accumulated in
+ * float64 (double-float per thread, fixed-order reduction).  Used to report
+ * the complex64 error against a complex128 run of the same circuit.  Both
+ * handles' streams are synchronised.  Synchronous. */
+LQS_API int lqs_sv_distance(lqs_sv* a, lqs_sv* b, double* diff2_host, double* norm2_b_host);
+
 /* Expectation value of H = sum_w coeff_w P_w (Listing 1: qml.expval(H)),
  * accumulated in float64 with deterministic two-stage reductions (no float
  * atomics).  *out_host = sum_w coeff_w <P_w>; per_term_host (optional,

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "arith.cuh"
 #include "lqs_internal.cuh"
@@ -136,11 +137,98 @@ __global__ void k_set_basis_d(double2* psi, uint64_t N, uint64_t x) {
     psi[i] = make_double2(i == x ? 1.0 : 0.0, 0.0);
 }
 
+// sum |a - b|^2 and sum |b|^2 for states of possibly different dtypes:
+// double-float per thread (chains of at most 64 terms), float64 per block.
+template <class SA, class SB>
+__global__ void k_distance(const SA* __restrict__ a, const SB* __restrict__ b, uint64_t N, double* part) {
+  __shared__ double r0[256], r1[256];
+  auto wd = [](const auto& v) -> DFC {
+    if constexpr (sizeof(v) == 8) return DFC{DF{v.x, 0.f}, DF{v.y, 0.f}};
+    else return DFC{d2df(v.x), d2df(v.y)};
+  };
+  double d0 = 0.0, d1 = 0.0;
+  DAcc x{0.f, 0.f}, y{0.f, 0.f};
+  int cnt = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const DFC va = wd(a[i]), vb = wd(b[i]);
+    const DF dr = df_sub(va.re, vb.re), di = df_sub(va.im, vb.im);
+    df_mac(x, dr, dr);
+    df_mac(x, di, di);
+    df_mac(y, vb.re, vb.re);
+    df_mac(y, vb.im, vb.im);
+    if (++cnt == 64) {
+      d0 += df2d(df_norm(x));
+      d1 += df2d(df_norm(y));
+      x = DAcc{0.f, 0.f};
+      y = DAcc{0.f, 0.f};
+      cnt = 0;
+    }
+  }
+  d0 += df2d(df_norm(x));
+  d1 += df2d(df_norm(y));
+  r0[threadIdx.x] = d0;
+  r1[threadIdx.x] = d1;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      r0[threadIdx.x] += r0[threadIdx.x + w];
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r0[0];
+    part[2 * blockIdx.x + 1] = r1[0];
+  }
+}
+
 }  // namespace lqs
 
 using namespace lqs;
 
 extern "C" {
+
+int lqs_sv_distance(lqs_sv* ha, lqs_sv* hb, double* diff2_host, double* norm2_b_host) {
+  LQS_TRY(check_sv(ha));
+  LQS_TRY(check_sv(hb));
+  if (!diff2_host || !norm2_b_host) return set_error(LQS_ERR_ARG, "output pointer is NULL");
+  SV* A = S_(ha);
+  SV* B = S_(hb);
+  if (A->n != B->n) return set_error(LQS_ERR_ARG, "states have different qubit counts");
+  LQS_CUDA_TRY(cudaStreamSynchronize(A->stream));
+  LQS_CUDA_TRY(cudaStreamSynchronize(B->stream));
+  const int grid = std::max(1, std::min<int>((int)std::min<uint64_t>((A->N() + 255) / 256, 1u << 20), A->sms * 4));
+  void* scratch = nullptr;
+  LQS_TRY(sv_scratch(B, 2, sizeof(double) * 2 * grid, &scratch));
+  double* part = static_cast<double*>(scratch);
+  cudaStream_t st = B->stream;
+  {
+    ProfScope ps(st, "k_distance", (double)(A->bytes() + B->bytes()), 0.0);
+    if (A->dtype == LQS_C64 && B->dtype == LQS_C64)
+      k_distance<float2, float2><<<grid, 256, 0, st>>>((const float2*)A->d, (const float2*)B->d, A->N(), part);
+    else if (A->dtype == LQS_C64)
+      k_distance<float2, double2><<<grid, 256, 0, st>>>((const float2*)A->d, (const double2*)B->d, A->N(), part);
+    else if (B->dtype == LQS_C64)
+      k_distance<double2, float2><<<grid, 256, 0, st>>>((const double2*)A->d, (const float2*)B->d, A->N(), part);
+    else
+      k_distance<double2, double2><<<grid, 256, 0, st>>>((const double2*)A->d, (const double2*)B->d, A->N(), part);
+    count_launch();
+  }
+  LQS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> h(2 * grid);
+  LQS_CUDA_TRY(cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
+  LQS_CUDA_TRY(cudaStreamSynchronize(st));
+  double d0 = 0.0, d1 = 0.0;
+  for (int i = 0; i < grid; ++i) {
+    d0 += h[2 * i];
+    d1 += h[2 * i + 1];
+  }
+  *diff2_host = d0;
+  *norm2_b_host = d1;
+  return LQS_OK;
+}
+
 
 const char* lqs_last_error(void) { return g_err.c_str(); }
 

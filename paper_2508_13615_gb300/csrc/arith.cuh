@@ -191,8 +191,22 @@ LQS_HD DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
 // ---------------------------------------------------------------------------
 // complex types per policy
 // ---------------------------------------------------------------------------
-struct __align__(16) DFC { DF re, im; };  // working complex (double-float), one 128-bit access
+struct DFC { DF re, im; };         // working complex (double-float); no alignment, so registers stay free
 struct DFK { DF re, im; };         // complex coefficient (double-float)
+
+// 128-bit shared-memory accesses of working amplitudes (the buffers are
+// 16-byte aligned per amplitude); other working types use plain accesses.
+LQS_HD void st_w(DFC* p, const DFC& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+}
+LQS_HD DFC ld_w(const DFC* p) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  return DFC{DF{f.x, f.y}, DF{f.z, f.w}};
+}
+LQS_HD void st_w(float2* p, const float2& v) { *p = v; }
+LQS_HD float2 ld_w(const float2* p) { return *p; }
+LQS_HD void st_w(double2* p, const double2& v) { *p = v; }
+LQS_HD double2 ld_w(const double2* p) { return *p; }
 
 struct ArF32 {
   using S = float2;  // storage amplitude
@@ -221,6 +235,7 @@ struct ArF32 {
   }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) { return make_float2(c0 * a.x + c1 * b.x, c0 * a.y + c1 * b.y); }
   static LQS_HD C kmul(C a, C b) { return cmul(a, b); }
+  static LQS_HD C cconst1() { return make_float2(1.f, 0.f); }
   static LQS_HD W neg(W a) { return make_float2(-a.x, -a.y); }
   static LQS_HD W mul_i(W a) { return make_float2(-a.y, a.x); }
   static LQS_HD W add(W a, W b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -260,6 +275,7 @@ struct ArF64 {
   }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) { return make_double2(c0 * a.x + c1 * b.x, c0 * a.y + c1 * b.y); }
   static LQS_HD C kmul(C a, C b) { return cmul(a, b); }
+  static LQS_HD C cconst1() { return make_double2(1.0, 0.0); }
   static LQS_HD W neg(W a) { return make_double2(dneg(a.x), dneg(a.y)); }
   static LQS_HD W mul_i(W a) { return make_double2(dneg(a.y), a.x); }
   static LQS_HD W add(W a, W b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -324,6 +340,7 @@ struct ArDF {
     const DFC r = cmul(a, DFC{b.re, b.im});
     return DFK{r.re, r.im};
   }
+  static LQS_HD C cconst1() { return DFK{DF{1.f, 0.f}, DF{0.f, 0.f}}; }
   static LQS_HD W neg(W a) { return DFC{df_neg(a.re), df_neg(a.im)}; }
   static LQS_HD W mul_i(W a) { return DFC{df_neg(a.im), a.re}; }
   static LQS_HD W add(W a, W b) { return DFC{df_add(a.re, b.re), df_add(a.im, b.im)}; }

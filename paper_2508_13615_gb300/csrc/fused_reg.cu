@@ -71,28 +71,39 @@ __device__ __forceinline__ void reg_apply(typename A::W (&v)[R], const TOp& o, c
   using C = typename A::C;
   if ((base & o.ecmask) != o.ecmask) return;  // a control outside the tile is 0
   const uint32_t lc = o.lcmask;
+  // Controls on local qubits are per-amplitude predicates; gates without them
+  // (most of them) take unpredicated code so no selects are spent.
   switch (o.kind) {
     case K_PHASE: {
       const C f = coef[o.coef];
 #pragma unroll
-      for (int e = 0; e < R; ++e)
+      for (int e = 0; e < R; ++e) {
         if (((jt | je[e]) & lc) == lc) v[e] = phase_apply<A>(f, o.special, v[e]);
+      }
       break;
     }
     case K_DIAG1: {
       const C d0 = coef[o.coef], d1 = coef[o.coef + 1];
-      if (o.l0 >= 0) {
-        const uint32_t tb = 1u << o.l0;
-#pragma unroll
-        for (int e = 0; e < R; ++e) {
-          const uint32_t j = jt | je[e];
-          if ((j & lc) == lc) v[e] = A::cmul((j & tb) ? d1 : d0, v[e]);
-        }
+      if (o.s0 >= 0 && lc == 0) {  // target in registers: a fixed pattern over the pairs
+        dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+          v[e0] = A::cmul(d0, v[e0]);
+          v[e1] = A::cmul(d1, v[e1]);
+        });
       } else {
-        const C d = (base & o.e0) ? d1 : d0;
+        // target on a thread bit or outside the tile: one factor per thread
+        const bool hi = o.l0 >= 0 ? ((jt >> o.l0) & 1u) != 0 : (base & o.e0) != 0;
+        if (o.s0 >= 0) {
+          dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+            if (((jt | je[e0]) & lc) != lc) return;
+            v[e0] = A::cmul(d0, v[e0]);
+            v[e1] = A::cmul(d1, v[e1]);
+          });
+        } else {
+          const C d = hi ? d1 : d0;
 #pragma unroll
-        for (int e = 0; e < R; ++e)
-          if (((jt | je[e]) & lc) == lc) v[e] = A::cmul(d, v[e]);
+          for (int e = 0; e < R; ++e)
+            if (((jt | je[e]) & lc) == lc) v[e] = A::cmul(d, v[e]);
+        }
       }
       break;
     }
@@ -110,17 +121,29 @@ __device__ __forceinline__ void reg_apply(typename A::W (&v)[R], const TOp& o, c
     case K_ANTI1: {
       const C f0 = coef[o.coef], f1 = coef[o.coef + 1];
       const bool plain = o.special == 1;
-      dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
-        if (((jt | je[e0]) & lc) != lc) return;
-        const W a = v[e0], b = v[e1];
-        if (plain) {
-          v[e0] = b;
-          v[e1] = a;
+      if (plain) {
+        if (lc == 0) {
+          dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+            const W a = v[e0];
+            v[e0] = v[e1];
+            v[e1] = a;
+          });
         } else {
+          dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+            if (((jt | je[e0]) & lc) != lc) return;
+            const W a = v[e0];
+            v[e0] = v[e1];
+            v[e1] = a;
+          });
+        }
+      } else {
+        dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+          if (((jt | je[e0]) & lc) != lc) return;
+          const W a = v[e0], b = v[e1];
           v[e0] = A::cmul(f0, b);
           v[e1] = A::cmul(f1, a);
-        }
-      });
+        });
+      }
       break;
     }
     case K_SWAP: {  // targets at slots 1 (t0) and 0 (t1)
@@ -135,23 +158,39 @@ __device__ __forceinline__ void reg_apply(typename A::W (&v)[R], const TOp& o, c
     }
     case K_DENSE1: {
       const C u00 = coef[o.coef], u01 = coef[o.coef + 1], u10 = coef[o.coef + 2], u11 = coef[o.coef + 3];
-      dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
-        if (((jt | je[e0]) & lc) != lc) return;
-        const W a = v[e0], b = v[e1];
-        v[e0] = A::cmac2(u00, a, u01, b);
-        v[e1] = A::cmac2(u10, a, u11, b);
-      });
+      if (lc == 0) {
+        dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+          const W a = v[e0], b = v[e1];
+          v[e0] = A::cmac2(u00, a, u01, b);
+          v[e1] = A::cmac2(u10, a, u11, b);
+        });
+      } else {
+        dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+          if (((jt | je[e0]) & lc) != lc) return;
+          const W a = v[e0], b = v[e1];
+          v[e0] = A::cmac2(u00, a, u01, b);
+          v[e1] = A::cmac2(u10, a, u11, b);
+        });
+      }
       break;
     }
     case K_DENSE1R: {
       const typename A::R u00 = CRe<A>::get(coef[o.coef]), u01 = CRe<A>::get(coef[o.coef + 1]),
                           u10 = CRe<A>::get(coef[o.coef + 2]), u11 = CRe<A>::get(coef[o.coef + 3]);
-      dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
-        if (((jt | je[e0]) & lc) != lc) return;
-        const W a = v[e0], b = v[e1];
-        v[e0] = A::rmac2(u00, a, u01, b);
-        v[e1] = A::rmac2(u10, a, u11, b);
-      });
+      if (lc == 0) {
+        dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+          const W a = v[e0], b = v[e1];
+          v[e0] = A::rmac2(u00, a, u01, b);
+          v[e1] = A::rmac2(u10, a, u11, b);
+        });
+      } else {
+        dispatch_pairs<A, R>(o.s0, [&](int e0, int e1) {
+          if (((jt | je[e0]) & lc) != lc) return;
+          const W a = v[e0], b = v[e1];
+          v[e0] = A::rmac2(u00, a, u01, b);
+          v[e1] = A::rmac2(u10, a, u11, b);
+        });
+      }
       break;
     }
     case K_DENSE2: {  // targets at slots 1 (t0, most significant) and 0 (t1)
@@ -175,11 +214,11 @@ __device__ __forceinline__ void reg_apply(typename A::W (&v)[R], const TOp& o, c
 #pragma unroll
       for (int m = 0; m < RLog<R>::r; ++m) regbits |= je[1 << m];
       // thread-bit factors (the amplitude's thread part is fixed per thread)
-      uint32_t rest = LF & ~regbits;
+      uint32_t rest = LF & ~regbits & jt;
       while (rest) {
         const int q = __ffs(rest) - 1;
         rest &= rest - 1;
-        if ((jt >> q) & 1u) acc = A::kmul(coef[o.coef + 1 + __popc(LF & ((1u << q) - 1u))], acc);
+        acc = A::kmul(coef[o.coef + 1 + __popc(LF & ((1u << q) - 1u))], acc);
       }
       uint64_t ef = o.e0;
       int ci = o.coef + 1 + __popc(LF);
@@ -189,19 +228,29 @@ __device__ __forceinline__ void reg_apply(typename A::W (&v)[R], const TOp& o, c
         if ((base >> q) & 1ull) acc = A::kmul(coef[ci], acc);
         ++ci;
       }
-      // register-bit factors: a doubling table over this thread's amplitudes
+      // register-bit factors: one per register slot (1 when the slot's qubit
+      // carries none), then a doubling table over this thread's amplitudes
+      C fm[RLog<R>::r];
+#pragma unroll
+      for (int m = 0; m < RLog<R>::r; ++m) {
+        const uint32_t qb = je[1 << m];
+        fm[m] = (LF & qb) ? coef[o.coef + 1 + __popc(LF & (qb - 1u))] : A::cconst1();
+      }
       C tab[R];
       tab[0] = acc;
 #pragma unroll
       for (int e = 1; e < R; ++e) {
         const int m = 31 - __clz(e);  // highest set bit of e
-        const uint32_t qb = je[1 << m];
-        if (LF & qb) tab[e] = A::kmul(coef[o.coef + 1 + __popc(LF & (qb - 1u))], tab[e ^ (1 << m)]);
-        else tab[e] = tab[e ^ (1 << m)];
+        tab[e] = A::kmul(fm[m], tab[e ^ (1 << m)]);
       }
+      if (lc == 0) {
 #pragma unroll
-      for (int e = 0; e < R; ++e)
-        if (((jt | je[e]) & lc) == lc) v[e] = A::cmul(tab[e], v[e]);
+        for (int e = 0; e < R; ++e) v[e] = A::cmul(tab[e], v[e]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < R; ++e)
+          if (((jt | je[e]) & lc) == lc) v[e] = A::cmul(tab[e], v[e]);
+      }
       break;
     }
     default:
@@ -282,11 +331,14 @@ __global__ void __launch_bounds__(kRegThreads) k_fused_reg(typename A::S* __rest
       if (o.kind == K_LAYOUT) {
         __syncthreads();  // readers of the previous exchange are done
 #pragma unroll
-        for (int e = 0; e < R; ++e) X1[swz<sizeof(S)>(jt | je[e])] = v[e];
+        for (int e = 0; e < R; ++e) st_w(&X1[swz<sizeof(S)>(jt | je[e])], v[e]);
         __syncthreads();
         set_layout<R>(o.ecmask, tid, G.k, jt, je);
 #pragma unroll
-        for (int e = 0; e < R; ++e) v[e] = X1[swz<sizeof(S)>(jt | je[e])];
+        for (int e = 0; e < R; ++e) v[e] = ld_w(&X1[swz<sizeof(S)>(jt | je[e])]);
+        // SWAPs since the previous exchange were relabellings: the read above
+        // went through them; from here on amplitudes carry their own labels
+        if (o.e0 != o.ecmask) set_layout<R>(o.e0, tid, G.k, jt, je);
       } else {
         reg_apply<A, R>(v, o, P.coef, base, jt, je);
       }
@@ -449,13 +501,29 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       if (std::find(slot.begin(), slot.end(), q) == slot.end()) p |= (uint64_t)q << (4 * sl++);
     return p;
   };
+  // Uncontrolled SWAPs move no data here: they relabel tile qubits.  pi[l] is
+  // the storage position of the amplitude bit that local qubit l denotes;
+  // every op is translated through pi, and the next exchange reads the tile
+  // through pi and resets it to the identity.
+  std::vector<int> pi(k);
+  for (int l = 0; l < k; ++l) pi[l] = l;
+  auto is_identity = [&]() {
+    for (int l = 0; l < k; ++l)
+      if (pi[l] != l) return false;
+    return true;
+  };
   auto emit_layout = [&](const std::vector<int>& slot) -> int {
     if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;  // the caller splits the segment
     TOp t{};
     t.kind = K_LAYOUT;
     t.gslot = -1;
-    t.ecmask = pack(slot);
+    const uint64_t logical = pack(slot);
+    uint64_t through = 0;  // the same layout with each position mapped through pi
+    for (int i = 0; i < k; ++i) through |= (uint64_t)pi[(logical >> (4 * i)) & 15] << (4 * i);
+    t.ecmask = through;
+    t.e0 = logical;
     P.op[P.nops++] = t;
+    for (int l = 0; l < k; ++l) pi[l] = l;
     return LQS_OK;
   };
   // Tiles arrive and leave in natural order (rows of contiguous amplitudes),
@@ -468,10 +536,28 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
   LQS_TRY(emit_layout(cur));
   for (size_t i = 0; i < seq.size(); ++i) {
     if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
+    if (seq[i].op >= 0) {
+      const KOp& so = ops[seq[i].op];
+      const int la = lp(so.t0), lb = lp(so.t1);
+      if (so.kind == K_SWAP && so.cmask == 0 && la >= 0 && lb >= 0) {
+        std::swap(pi[la], pi[lb]);
+        continue;
+      }
+    }
+    // storage position of local qubit q (after relabelling SWAPs), -1 outside the tile
+    auto pp = [&](int q) -> int {
+      const int l = lp(q);
+      return l < 0 ? -1 : pi[l];
+    };
     if (seq[i].group >= 0) {
       const DGroup& g = groups[seq[i].group];
       auto f = g.f;
-      std::sort(f.begin(), f.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      // local factors in increasing storage position, then outside factors by qubit
+      std::sort(f.begin(), f.end(), [&](const auto& x, const auto& y) {
+        const int a = pp(x.first), b = pp(y.first);
+        if ((a < 0) != (b < 0)) return a >= 0;
+        return a >= 0 ? a < b : x.first < y.first;
+      });
       TOp t{};
       t.kind = K_DPROD;
       t.gslot = -1;
@@ -479,7 +565,7 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       t.s0 = t.s1 = -1;
       for (int q = 0; q < G.n; ++q) {
         if (!((g.cond >> q) & 1)) continue;
-        const int l = lp(q);
+        const int l = pp(q);
         if (l >= 0) t.lcmask |= 1u << l;
         else t.ecmask |= 1ull << q;
       }
@@ -488,15 +574,10 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       t.coef = (int16_t)P.ncoef;
       P.coef[P.ncoef++] = A::cconst(g.C.real(), g.C.imag());
       uint64_t lf = 0, ef = 0;
-      for (auto& x : f) {  // local factors first (increasing local position = increasing qubit)
-        const int l = lp(x.first);
-        if (l < 0) continue;
-        lf |= 1ull << l;
-        P.coef[P.ncoef++] = A::cconst(x.second.real(), x.second.imag());
-      }
-      for (auto& x : f) {  // then factors on qubits outside the tile
-        if (lp(x.first) >= 0) continue;
-        ef |= 1ull << x.first;
+      for (auto& x : f) {
+        const int l = pp(x.first);
+        if (l >= 0) lf |= 1ull << l;
+        else ef |= 1ull << x.first;
         P.coef[P.ncoef++] = A::cconst(x.second.real(), x.second.imag());
       }
       t.e1 = lf;
@@ -506,24 +587,37 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
     }
     const KOp& o = ops[seq[i].op];
     if (!o.diagonal()) {
-      const int a = lp(o.t0), b = lp(o.t1);
+      const int a = pp(o.t0), b = pp(o.t1);
       const bool fits = two_target(o) ? (cur[1] == a && cur[0] == b)
                                       : std::find(cur.begin(), cur.end(), a) != cur.end();
       if (!fits) {
         cur = choose(i);
-        LQS_TRY(emit_layout(cur));
+        LQS_TRY(emit_layout(cur));  // resets the relabelling
         if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
       }
     }
     const int rc = add_tile_op(P, o, -1);
     if (rc != LQS_OK) return LQS_ERR_UNSUPPORTED;
     TOp& t = P.op[P.nops - 1];
+    if (!is_identity()) {  // translate the op's local positions to storage positions
+      if (t.l0 >= 0) t.l0 = (int8_t)pi[t.l0];
+      if (t.l1 >= 0) t.l1 = (int8_t)pi[t.l1];
+      uint32_t lc = 0;
+      for (int l = 0; l < k; ++l)
+        if ((t.lcmask >> l) & 1u) lc |= 1u << pi[l];
+      t.lcmask = lc;
+    }
+    t.s0 = t.s1 = -1;
+    if (o.kind == K_DIAG1 && t.l0 >= 0) {  // a diagonal target held in registers
+      const auto it = std::find(cur.begin(), cur.end(), (int)t.l0);
+      if (it != cur.end()) t.s0 = (int8_t)(it - cur.begin());
+    }
     if (!o.diagonal()) {
-      t.s0 = (int8_t)(std::find(cur.begin(), cur.end(), lp(o.t0)) - cur.begin());
-      t.s1 = o.t1 >= 0 ? (int8_t)(std::find(cur.begin(), cur.end(), lp(o.t1)) - cur.begin()) : (int8_t)-1;
+      t.s0 = (int8_t)(std::find(cur.begin(), cur.end(), pp(o.t0)) - cur.begin());
+      t.s1 = o.t1 >= 0 ? (int8_t)(std::find(cur.begin(), cur.end(), pp(o.t1)) - cur.begin()) : (int8_t)-1;
     }
   }
-  if (cur != natural) LQS_TRY(emit_layout(natural));
+  if (cur != natural || !is_identity()) LQS_TRY(emit_layout(natural));
   return LQS_OK;
 }
 

@@ -25,6 +25,7 @@
 #include "lqs_internal.cuh"
 #include "tile.cuh"
 #include "tile_ops.cuh"
+#include "measure_common.cuh"
 
 namespace lqs {
 
@@ -32,54 +33,8 @@ template <class A> int add_tile_op(TileProg<A>& P, const KOp& o, int gslot);
 template <class A> void init_prog(TileProg<A>& P, int n, uint64_t Q, int k, int b);
 
 // ---------------------------------------------------------------------------
-// double-float views of the working amplitudes
-// ---------------------------------------------------------------------------
-LQS_HD DFC to_dfc(const float2& w) { return DFC{DF{w.x, 0.f}, DF{w.y, 0.f}}; }
-LQS_HD DFC to_dfc(const double2& w) { return DFC{d2df(w.x), d2df(w.y)}; }
-LQS_HD DFC to_dfc(const DFC& w) { return w; }
-
-// Re(conj(a) b) and Im(conj(a) b) accumulated with a sign.
-__device__ __forceinline__ void acc_re_conj(DAcc& A, const DFC& a, const DFC& b, bool neg) {
-  const DF ar = neg ? df_neg(a.re) : a.re, ai = neg ? df_neg(a.im) : a.im;
-  df_mac(A, ar, b.re);
-  df_mac(A, ai, b.im);
-}
-__device__ __forceinline__ void acc_im_conj(DAcc& A, const DFC& a, const DFC& b, bool neg) {
-  const DF ar = neg ? df_neg(a.re) : a.re, ai = neg ? a.im : df_neg(a.im);
-  df_mac(A, ar, b.im);
-  df_mac(A, ai, b.re);
-}
-
-__device__ __forceinline__ DF shfl_df(DF v, int off) {
-  return DF{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
-}
-// Warp sum of a double-float accumulator; the result is valid in every lane.
-__device__ __forceinline__ DF warp_sum(DAcc a) {
-  DF v = df_norm(a);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = df_add(v, shfl_df(v, off));
-  return v;
-}
-
-// ---------------------------------------------------------------------------
 // Pauli-word passes
 // ---------------------------------------------------------------------------
-constexpr int kPassWords = 24;
-
-struct PWord {
-  uint32_t xl, zl;   // local X and Z masks
-  uint64_t ze;       // Z bits outside the tile (a per-tile sign)
-  uint32_t ph;       // number of Y factors mod 4 (phase i^ph)
-  int lowbit;        // lowest local bit of xl (-1: diagonal word)
-  DF c;              // coefficient (for lambda)
-};
-
-struct PauliProg {
-  TileGeom g;
-  int nw;
-  PWord w[kPassWords];
-};
-
 // Per-thread double-float partial sums (one per word, in shared memory) are
 // flushed every kFlushTiles tiles: warp sum in double-float, then float64
 // per warp.  A chain holds at most kFlushTiles * (tile amplitudes / threads)
@@ -111,7 +66,9 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
   V* LT = reinterpret_cast<V*>(lbuf);
   double* wacc = reinterpret_cast<double*>(smem_raw + (size_t)nt * sizeof(S) * (kLam ? 2 : 1));
   DAcc* sacc = reinterpret_cast<DAcc*>(wacc + kTileWarps * kPassWords);  // [word][thread]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sacc + kPassWords * kTileThreads);
+  PWord* words = reinterpret_cast<PWord*>(sacc + kPassWords * kTileThreads);  // staged copy of P.w
+  uint64_t* bar = reinterpret_cast<uint64_t*>(words + kPassWords);
+  for (int w = threadIdx.x; w < P.nw; w += blockDim.x) words[w] = P.w[w];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kTileWarps * kPassWords; i += blockDim.x) wacc[i] = 0.0;
   for (int w = 0; w < kPassWords; ++w) sacc[w * kTileThreads + threadIdx.x] = DAcc{0.f, 0.f};
@@ -123,7 +80,7 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
   auto flush = [&]() {
     for (int w = 0; w < P.nw; ++w) {
       const DF s = warp_sum(sacc[w * kTileThreads + threadIdx.x]);
-      if (lane == 0) wacc[warp * kPassWords + w] += (P.w[w].lowbit >= 0 ? 2.0 : 1.0) * df2d(s);
+      if (lane == 0) wacc[warp * kPassWords + w] += (words[w].lowbit >= 0 ? 2.0 : 1.0) * df2d(s);
       sacc[w * kTileThreads + threadIdx.x] = DAcc{0.f, 0.f};
     }
   };
@@ -167,7 +124,7 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
         }
       }
       for (int w = 0; w < P.nw; ++w) {
-        const PWord& Wd = P.w[w];
+        const PWord& Wd = words[w];
         DAcc a = sacc[w * kTileThreads + threadIdx.x];
         const bool tneg = __popcll(base & Wd.ze) & 1;
         if (Wd.lowbit < 0) {
@@ -212,7 +169,7 @@ __global__ void __launch_bounds__(kTileThreads) k_pauli(const typename A::S* __r
         }
 #pragma unroll 1
         for (int w = 0; w < P.nw; ++w) {
-          const PWord& Wd = P.w[w];
+          const PWord& Wd = words[w];
           const uint32_t src = j ^ Wd.xl;
           const DFC v = to_dfc(T[src]);
           const bool neg = ((__popcll(base & Wd.ze) + __popc(src & Wd.zl)) & 1) != 0;
@@ -325,62 +282,6 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
   if (threadIdx.x == 0) out[i] = sh[0];
 }
 
-// Group words into passes: X masks must fit a tile of k qubits (low b qubits
-// plus chosen high qubits); at most kPassWords words per pass.  Words whose
-// X/Y qubits cannot fit any tile go to `wide` (global pair passes).
-struct PassPlan {
-  uint64_t Q;
-  std::vector<int> words;
-};
-static int plan_passes(int n, const lqs_pauli* terms, int n_terms, int k, int b, std::vector<PassPlan>& out,
-                       std::vector<int>& wide) {
-  std::vector<char> done(n_terms, 0);
-  int left = n_terms;
-  const uint64_t low = (b >= 64) ? ~0ull : ((1ull << b) - 1);
-  for (int i = 0; i < n_terms; ++i)
-    if (__builtin_popcountll(terms[i].x_mask | low) > k) {
-      wide.push_back(i);
-      done[i] = 1;
-      --left;
-    }
-  while (left) {
-    PassPlan p;
-    p.Q = low;
-    for (int i = 0; i < n_terms && (int)p.words.size() < kPassWords; ++i) {
-      if (done[i]) continue;
-      const uint64_t need = terms[i].x_mask & ~p.Q;
-      if (__builtin_popcountll(p.Q | need) <= k) {
-        p.Q |= need;
-        p.words.push_back(i);
-        done[i] = 1;
-        --left;
-      }
-    }
-    if (p.words.empty()) return set_error(LQS_ERR_ARG, "internal: Pauli pass planner made no progress");
-    for (int q = b; q < n && __builtin_popcountll(p.Q) < k; ++q) p.Q |= 1ull << q;
-    out.push_back(std::move(p));
-  }
-  return LQS_OK;
-}
-
-static TileGeom geom_for(int n, uint64_t Q, int k, int b, size_t amp) {
-  TileGeom G{};
-  G.n = n;
-  G.k = k;
-  G.b = b;
-  for (int q = b; q < n; ++q)
-    if ((Q >> q) & 1) G.h[G.r++] = q;
-  G.ntiles = 1ull << (n - k);
-  G.row_bytes = (uint32_t)(amp << b);
-  return G;
-}
-static int lpos(const TileGeom& G, int q) {
-  if (q < G.b) return q;
-  for (int m = 0; m < G.r; ++m)
-    if (G.h[m] == q) return G.b + m;
-  return -1;
-}
-
 // Tile size for measurement passes: smaller than the fused default so that
 // two tiles (psi and lambda) plus accumulators leave room for 2-3 CTAs per SM.
 static void measure_kb(int n, int dtype, int& k, int& b) {
@@ -391,7 +292,7 @@ static void measure_kb(int n, int dtype, int& k, int& b) {
 
 static size_t pauli_smem(size_t amp, int k, bool lam) {
   return (amp << k) * (lam ? 2 : 1) + sizeof(double) * kTileWarps * kPassWords +
-         sizeof(DAcc) * kPassWords * kTileThreads + 16;
+         sizeof(DAcc) * kPassWords * kTileThreads + sizeof(PWord) * kPassWords + 16;
 }
 
 template <class A, int MODE>
@@ -444,8 +345,10 @@ static int pauli_passes(SV* sv, const lqs_pauli* terms, int n_terms, void* lam, 
   // partial sums: one slot per word per block, laid out pass by pass
   const uint64_t ntiles = 1ull << (sv->n - k);
   const size_t amp = sizeof(typename A::S);
-  const size_t smem2 = pauli_smem(amp, k, true);
-  const int grid = occupancy_grid<A>(sv, (const void*)k_pauli<A, 3>, smem2, ntiles);
+  for (const void* fn : {(const void*)k_pauli<A, 1>, (const void*)k_pauli<A, 3>, (const void*)k_pauli<A, 7>})
+    LQS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  const int grid = lam ? occupancy_grid<A>(sv, (const void*)k_pauli<A, 3>, pauli_smem(amp, k, true), ntiles)
+                       : occupancy_grid<A>(sv, (const void*)k_pauli<A, 1>, pauli_smem(amp, k, false), ntiles);
   const int wgrid = (int)std::min<uint64_t>(std::max<uint64_t>(sv->N() / 2 / 256, 1), (uint64_t)std::max(sv->sms, 1) * 8);
   size_t slots = 0;
   for (auto& p : passes) slots += p.words.size();
@@ -560,45 +463,6 @@ int run_norm2(SV* sv, int arith, double* out) {
 // ---------------------------------------------------------------------------
 // adjoint sweep
 // ---------------------------------------------------------------------------
-constexpr int kMaxGradSlots = 128;
-
-// Im <lambda|G|psi> over the tile for generator G of op o (before U^dagger).
-template <class A>
-__device__ __forceinline__ DAcc gen_partial(const typename A::W* Ps, const typename A::W* Ls, const TOp& o,
-                                            uint64_t base, int k) {
-  DAcc acc{0.f, 0.f};
-  const uint32_t tid = threadIdx.x, nth = blockDim.x;
-  const uint32_t lc = o.lcmask;
-  if (o.gen == G_P1 || (o.gen == G_Z && o.l0 < 0)) {
-    // single amplitudes: P1 on the op's control set, or Z on a qubit outside
-    // the tile (a per-tile sign)
-    const bool neg = (o.gen == G_Z) && (base & o.e0);
-    const uint32_t ng = 1u << (k - o.nfix);
-    for (uint32_t g = tid; g < ng; g += nth) {
-      const uint32_t j = ins0(g, o.fix, o.nfix) | lc;
-      acc_im_conj(acc, to_dfc(Ls[j]), to_dfc(Ps[j]), neg);
-    }
-    return acc;
-  }
-  const uint32_t tb = 1u << o.l0;
-  const uint32_t ng = 1u << (k - o.nfix);
-  for (uint32_t g = tid; g < ng; g += nth) {
-    const uint32_t j0 = ins0(g, o.fix, o.nfix) | lc, j1 = j0 | tb;
-    const DFC p0 = to_dfc(Ps[j0]), p1 = to_dfc(Ps[j1]), l0 = to_dfc(Ls[j0]), l1 = to_dfc(Ls[j1]);
-    if (o.gen == G_X) {  // conj(l0) p1 + conj(l1) p0
-      acc_im_conj(acc, l0, p1, false);
-      acc_im_conj(acc, l1, p0, false);
-    } else if (o.gen == G_Y) {  // conj(l0)(-i p1) + conj(l1)(i p0)
-      acc_re_conj(acc, l0, p1, true);
-      acc_re_conj(acc, l1, p0, false);
-    } else {  // G_Z: conj(l0) p0 - conj(l1) p1
-      acc_im_conj(acc, l0, p0, false);
-      acc_im_conj(acc, l1, p1, true);
-    }
-  }
-  return acc;
-}
-
 template <class A>
 __global__ void __launch_bounds__(kTileThreads) k_adjoint(typename A::S* __restrict__ psi,
                                                           typename A::S* __restrict__ lam,
@@ -684,45 +548,6 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint(typename A::S* __restr
     for (int q = 0; q < kTileWarps; ++q) v += wacc[q * kMaxGradSlots + s];
     partial[(size_t)s * gridDim.x + blockIdx.x] = v;
   }
-}
-
-// U^dagger of a lowered op (same kernel class, conjugate-transposed entries).
-static KOp inverse_op(const KOp& o) {
-  KOp r = o;
-  auto conj_at = [&](int i) { r.m[2 * i + 1] = -r.m[2 * i + 1]; };
-  switch (o.kind) {
-    case K_PHASE:
-      conj_at(0);
-      if (o.special == 2) r.special = 3;
-      else if (o.special == 3) r.special = 2;
-      break;
-    case K_DIAG1: conj_at(0); conj_at(1); break;
-    case K_DIAG2: for (int i = 0; i < 4; ++i) conj_at(i); break;
-    case K_ANTI1:  // [[0, f0], [f1, 0]]^dagger = [[0, conj f1], [conj f0, 0]]
-      r.m[0] = o.m[2]; r.m[1] = -o.m[3];
-      r.m[2] = o.m[0]; r.m[3] = -o.m[1];
-      break;
-    case K_SWAP: break;
-    case K_DENSE1:
-      for (int rr = 0; rr < 2; ++rr)
-        for (int c = 0; c < 2; ++c) {
-          r.m[2 * (2 * rr + c)] = o.m[2 * (2 * c + rr)];
-          r.m[2 * (2 * rr + c) + 1] = -o.m[2 * (2 * c + rr) + 1];
-        }
-      break;
-    case K_DENSE1R:
-      r.m[1] = o.m[2];
-      r.m[2] = o.m[1];
-      break;
-    case K_DENSE2:
-      for (int rr = 0; rr < 4; ++rr)
-        for (int c = 0; c < 4; ++c) {
-          r.m[2 * (4 * rr + c)] = o.m[2 * (4 * c + rr)];
-          r.m[2 * (4 * rr + c) + 1] = -o.m[2 * (4 * c + rr) + 1];
-        }
-      break;
-  }
-  return r;
 }
 
 template <class A>

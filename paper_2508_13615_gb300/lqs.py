@@ -99,6 +99,7 @@ def _load():
         "lqs_kernel_launches": (u64, []),
         "lqs_debug_df_roundtrip": (i32, [dp, dp, i64]),
         "lqs_expval_static": (i32, [vp, i32, i32, vp, ctypes.POINTER(lqs_pauli), i32, dp, dp]),
+        "lqs_sv_distance": (i32, [vp, vp, dp, dp]),
         "lqs_profile_start": (i32, []),
         "lqs_profile_stop": (i32, [ctypes.POINTER(lqs_launch_record), i32, ip]),
     }
@@ -383,3 +384,10 @@ def lqs_expval_static(psi_device_ptr: int, n_qubits: int, dtype, terms, cuda_str
     _check(_L.lqs_expval_static(ctypes.c_void_p(psi_device_ptr), int(n_qubits), _dtype_code(dtype), cuda_stream,
                                 pa.ptr(), pa.n, ctypes.byref(out), _dptr(per)))
     return out.value, per[: pa.n]
+
+
+def lqs_sv_distance(ha, hb) -> Tuple[float, float]:
+    """(sum |a-b|^2, sum |b|^2) in float64."""
+    d, nb = ctypes.c_double(), ctypes.c_double()
+    _check(_L.lqs_sv_distance(ha, hb, ctypes.byref(d), ctypes.byref(nb)))
+    return d.value, nb.value

@@ -1,0 +1,56 @@
+"""Batched circuits (one persistent launch) vs the oracle and vs one-at-a-time."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import set_mode
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(seed=3, count=10, nmin=2, nmax=14):
+    r = W.splitmix64(seed, 0, 2 * count)
+    out = []
+    for i in range(count):
+        n = nmin + int(r[2 * i] % np.uint64(nmax - nmin + 1))
+        L = 1 + int(r[2 * i + 1] % np.uint64(3))
+        out.append(W.ansatz(n, L, seed + 10 * i))
+    return out
+
+
+@pytest.mark.parametrize("dtype,arith,tol", [("c128", "df", 1e-10), ("c128", "f64", 1e-10), ("c64", "f32", 5e-4)])
+def test_batch_matches_oracle(dtype, arith, tol):
+    import paper_2508_13615_gb300 as L
+    set_mode(arith)
+    circs = small_batch() + [W.ansatz(13, 2, 5), W.ansatz(14, 1, 6)]  # several tiles each
+    terms = [W.tfim(c.n_qubits) for c in circs]
+    e, g = L.lqs_batch_run(circs, terms, dtype)
+    for c, t, ei, gi in zip(circs, terms, e, g):
+        assert abs(ei - oracle.energy(c, t)) <= tol
+        np.testing.assert_allclose(gi, oracle.param_shift_grad(c, t), atol=tol)
+
+
+def test_batch_equals_one_at_a_time():
+    import paper_2508_13615_gb300 as L
+    set_mode("df")
+    circs = small_batch(seed=11, count=16, nmin=8, nmax=16)
+    terms = [W.tfim(c.n_qubits) + [W.pauli_word(0.3, {0: "Y", 1: "Y"})] for c in circs]
+    e, g = L.lqs_batch_run(circs, terms, "c64")
+    for c, t, ei, gi in zip(circs, terms, e, g):
+        with L.StateVector(c.n_qubits, "c64") as sv:
+            sv.set_basis(0)
+            sv.apply(c, fused=True)
+            g1, e1 = sv.adjoint_grad(c, t)
+        assert abs(ei - e1) <= 1e-5
+        np.testing.assert_allclose(gi, g1, atol=1e-4)
+
+
+def test_batch_energy_only_and_ragged_edge_cases():
+    import paper_2508_13615_gb300 as L
+    set_mode("df")
+    circs = [W.ansatz(1, 1, 1), W.Circuit(3), W.ghz(5), W.qft(6)]  # one qubit, no gates, no parameters
+    terms = [[W.pauli_word(1.0, {0: "Z"})], W.tfim(3), W.zz_chain(5), W.tfim(6)]
+    e, g = L.lqs_batch_run(circs, terms, "c128", grads=False)
+    for c, t, ei in zip(circs, terms, e):
+        assert abs(ei - oracle.energy(c, t)) <= 1e-12
