@@ -272,6 +272,44 @@ LQS_API int lqs_set_arith(int arith);
 /* Number of kernels this library has launched since load (for accounting). */
 LQS_API uint64_t lqs_kernel_launches(void);
 
+/* ---- compiled segments ----------------------------------------------------------- *
+ * The fused path applies each segment of a circuit (the gates that share one pass of
+ * tiles through on-chip memory; Sec. 2's "local" gates, see lqs_apply_fused) with a
+ * register-tile kernel.  That kernel can run in two forms with the same arithmetic:
+ *   - the interpreter: one precompiled kernel reads the segment's op list at run time;
+ *   - a compiled segment: the op list written out as straight-line CUDA C++ (register
+ *     slots, control patterns and coefficient offsets constant) and compiled at run
+ *     time for sm_103a with NVRTC (libnvrtc.so.13, found by dlopen; the environment
+ *     variable LQS_NVRTC may name it).
+ * Compiled segments are cached per structure (not per angle: coefficients stay kernel
+ * parameters) and device for the life of the process.
+ * Modes: LQS_JIT_OFF never compiles; LQS_JIT_ON compiles every segment at its first use;
+ * LQS_JIT_AUTO (default, or the environment variable LQS_JIT=0/1/2 at load) compiles a
+ * structure at its second use on states of 20 or more qubits, running the interpreter
+ * before that.  A call compiles the structures it needs on up to 8 host threads before
+ * its first launch.  When NVRTC is missing, LQS_JIT_ON makes lqs_apply_fused fail with
+ * LQS_ERR_UNSUPPORTED and LQS_JIT_AUTO keeps the interpreter (lqs_jit_info reports it). */
+typedef enum { LQS_JIT_OFF = 0, LQS_JIT_ON = 1, LQS_JIT_AUTO = 2 } lqs_jit_mode;
+LQS_API int lqs_set_jit(int mode);
+typedef struct {
+  int mode;                /* current lqs_jit_mode */
+  int compiled;            /* structures compiled since load */
+  int failed;              /* structures NVRTC rejected (the interpreter runs them) */
+  int cached;              /* structures seen (compiled or not) */
+  uint64_t launches;       /* compiled-segment launches since load */
+  double compile_seconds;  /* host time spent in NVRTC, summed over threads */
+  char last_error[256];    /* last compile or load failure ("" if none) */
+} lqs_jit_stats;
+LQS_API int lqs_jit_info(lqs_jit_stats* out);
+/* Compiles, without a GPU, every segment structure lqs_apply_fused would launch for this
+ * circuit on an n-qubit state of `dtype` with arithmetic `arith` (lqs_arith) and `cfg`
+ * (may be NULL), whatever the mode; *n_compiled (may be NULL) gets the number of
+ * structures compiled by this call.  Lets a caller pay the compile cost ahead of a timed
+ * or latency-critical loop.  Errors as lqs_apply_fused, plus LQS_ERR_UNSUPPORTED when
+ * NVRTC cannot be loaded or rejects a segment (lqs_last_error has its log). */
+LQS_API int lqs_jit_precompile(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops,
+                               const double* params, int n_params, const lqs_fuse_cfg* cfg, int* n_compiled);
+
 /* Per-launch profile records (tracing).  Between lqs_profile_start and
  * lqs_profile_stop every kernel the library launches is bracketed by CUDA
  * events on its stream; stop synchronises those streams and returns, per

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "arith.cuh"
+#include "jit.h"
 #include "lqs_internal.cuh"
 
 namespace lqs {
@@ -416,7 +417,39 @@ int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* param
   LQS_TRY(resolve_cfg(sv->n, sv->dtype, cfg, pc, &arith));
   std::vector<Segment> segs;
   LQS_TRY(plan_segments(sv->n, kops, pc, segs));
+  if (jit_enabled_for(sv->n)) {  // compile the structures this call needs, in parallel, before launching
+    std::vector<void*> todo;
+    for (const Segment& s : segs) LQS_TRY(jit_collect(sv->n, sv->dtype, arith, kops, s, pc, false, todo));
+    const int rc = jit_compile(todo);
+    if (rc != LQS_OK && jit_mode() == LQS_JIT_ON) return rc;
+  }
   for (const Segment& s : segs) LQS_TRY(launch_segment(sv, kops, s, pc, arith));
+  return LQS_OK;
+}
+
+int lqs_jit_precompile(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops, const double* params,
+                       int n_params, const lqs_fuse_cfg* cfg, int* n_compiled) {
+  if (n_compiled) *n_compiled = 0;
+  if (n_qubits < 1 || n_qubits > 36) return set_error(LQS_ERR_ARG, "n_qubits must be in [1, 36]");
+  if (dtype != LQS_C64 && dtype != LQS_C128) return set_error(LQS_ERR_ARG, "bad dtype");
+  if (arith != LQS_ARITH_AUTO && arith != LQS_ARITH_F64 && arith != LQS_ARITH_DF)
+    return set_error(LQS_ERR_ARG, "arith must be LQS_ARITH_AUTO, LQS_ARITH_F64 or LQS_ARITH_DF");
+  std::vector<KOp> kops;
+  LQS_TRY(lower_ops(n_qubits, ops, n_ops, params, n_params, false, kops));
+  PlanCfg pc;
+  int ar = LQS_ARITH_AUTO;
+  LQS_TRY(resolve_cfg(n_qubits, dtype, cfg, pc, &ar));
+  if (arith != LQS_ARITH_AUTO) ar = arith;
+  std::vector<Segment> segs;
+  LQS_TRY(plan_segments(n_qubits, kops, pc, segs));
+  std::vector<void*> todo;
+  for (const Segment& s : segs) LQS_TRY(jit_collect(n_qubits, dtype, ar, kops, s, pc, true, todo));
+  LQS_TRY(jit_compile(todo));
+  int ok = 0;
+  std::string err;
+  const int st = jit_states(todo, &ok, &err);
+  if (n_compiled) *n_compiled = ok;
+  if (st != LQS_OK) return set_error(LQS_ERR_UNSUPPORTED, "segment compilation failed: " + err);
   return LQS_OK;
 }
 

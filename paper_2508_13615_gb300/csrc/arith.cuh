@@ -16,8 +16,10 @@
 // Every error-free step uses the explicitly rounded intrinsics (__fadd_rn,
 // __fmul_rn, __fmaf_rn) so the compiler cannot contract or reassociate them.
 #pragma once
+#ifndef __CUDACC_RTC__  // runtime-compiled segment kernels bring their own integer types
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace lqs {
 
@@ -139,12 +141,14 @@ LQS_HD double df2d(DF v) { return f2d_bits(v.h) + f2d_bits(v.l); }
 
 // Split a double into a double-float constant: hi = RN(x), lo = RN(x - hi).
 // Host-side (coefficients are split once when a gate is prepared).
+#ifndef __CUDACC_RTC__
 inline DF split_const(double x) {
   DF r;
   r.h = (float)x;
   r.l = (float)(x - (double)r.h);
   return r;
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // double-float arithmetic
@@ -292,8 +296,10 @@ struct ArDF {
   using C = DFK;
   using R = DF;
   static constexpr int kAmpBytes = 16;
+#ifndef __CUDACC_RTC__  // host-side coefficient preparation
   static inline C cconst(double re, double im) { return DFK{split_const(re), split_const(im)}; }
   static inline R rconst(double x) { return split_const(x); }
+#endif
   static LQS_HD W load(const S& s) { return DFC{d2df(s.x), d2df(s.y)}; }
   static LQS_HD S store(W w) { return make_double2(df2d(w.re), df2d(w.im)); }
   static LQS_HD W zero() { return DFC{DF{0.f, 0.f}, DF{0.f, 0.f}}; }

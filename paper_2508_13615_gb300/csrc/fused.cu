@@ -301,6 +301,24 @@ int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, cons
   return launch_fused_t<ArDF>(sv, ops, seg, pc, arith);
 }
 
+// Mirrors launch_segment's routing and splitting without launching: each
+// register-tile program the segment will run is noted for the segment
+// compiler (and queued for compilation when the mode asks, or `force`).
+int jit_collect(int n, int dtype, int arith, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc,
+                bool force, std::vector<void*>& todo) {
+  if (seg.ops.size() == 1) return LQS_OK;
+  const int k = std::min(pc.k, n), b = std::min(pc.b, k);
+  if (k != reg_tile_qubits(dtype)) return LQS_OK;
+  const int rc = note_reg_prog(n, dtype, arith, ops, seg, k, b, force, todo);
+  if (rc != LQS_ERR_UNSUPPORTED) return rc;
+  Segment lo, hi;
+  lo.qmask = hi.qmask = seg.qmask;
+  lo.ops.assign(seg.ops.begin(), seg.ops.begin() + seg.ops.size() / 2);
+  hi.ops.assign(seg.ops.begin() + seg.ops.size() / 2, seg.ops.end());
+  LQS_TRY(jit_collect(n, dtype, arith, ops, lo, pc, force, todo));
+  return jit_collect(n, dtype, arith, ops, hi, pc, force, todo);
+}
+
 // explicit instantiations used by the measurement kernels
 template int add_tile_op<ArF32>(TileProg<ArF32>&, const KOp&, int);
 template int add_tile_op<ArF64>(TileProg<ArF64>&, const KOp&, int);

@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "jit.h"
 #include "lqs_internal.cuh"
 #include "tile.cuh"
 #include "tile_ops.cuh"
@@ -628,6 +629,14 @@ int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, 
   static thread_local TileProg<A> P;
   init_prog(P, sv->n, seg.qmask, k, b);
   LQS_TRY(build_reg_prog(P, ops, seg, r));
+  double flops = 0.0;
+  for (int i : seg.ops) flops += kop_touched_fraction(ops[i]) * kop_flops_per_amp(ops[i]);
+  {
+    bool launched = false;
+    const std::string jname = std::string("k_fused_reg_jit/") + arith_tag(sv->dtype, arith);
+    LQS_TRY(jit_launch(P, r, sv, 2.0 * (double)sv->bytes(), flops * (double)sv->N(), jname.c_str(), &launched));
+    if (launched) return LQS_OK;
+  }
   const size_t smem = 2 * ((size_t)sizeof(typename A::S) << k) + 16;
   static bool attr_done = false;
   if (!attr_done) {
@@ -638,8 +647,6 @@ int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, 
   LQS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_reg<A, R>, kRegThreads, smem));
   per_sm = std::max(per_sm, 1);
   const uint64_t grid = std::min<uint64_t>(P.g.ntiles, (uint64_t)std::max(sv->sms, 1) * per_sm);
-  double flops = 0.0;
-  for (int i : seg.ops) flops += kop_touched_fraction(ops[i]) * kop_flops_per_amp(ops[i]);
   const std::string pname = std::string("k_fused_reg/") + arith_tag(sv->dtype, arith);
   ProfScope ps(sv->stream, pname.c_str(), 2.0 * (double)sv->bytes(), flops * (double)sv->N());
   k_fused_reg<A, R><<<(unsigned)grid, kRegThreads, smem, sv->stream>>>(static_cast<typename A::S*>(sv->d), P,
@@ -647,6 +654,23 @@ int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, 
   count_launch();
   LQS_CUDA_TRY(cudaGetLastError());
   return LQS_OK;
+}
+
+template <class A>
+static int note_reg_prog_t(int n, const std::vector<KOp>& ops, const Segment& seg, int k, int b, bool force,
+                           std::vector<void*>& todo) {
+  constexpr int R = RegR<A>::R;
+  static thread_local TileProg<A> P;
+  init_prog(P, n, seg.qmask, k, b);
+  LQS_TRY(build_reg_prog(P, ops, seg, RLog<R>::r));
+  return jit_note(P, RLog<R>::r, n, force, todo);
+}
+
+int note_reg_prog(int n, int dtype, int arith, const std::vector<KOp>& ops, const Segment& seg, int k, int b,
+                  bool force, std::vector<void*>& todo) {
+  if (dtype == LQS_C64) return note_reg_prog_t<ArF32>(n, ops, seg, k, b, force, todo);
+  if (arith == LQS_ARITH_F64) return note_reg_prog_t<ArF64>(n, ops, seg, k, b, force, todo);
+  return note_reg_prog_t<ArDF>(n, ops, seg, k, b, force, todo);
 }
 
 int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {

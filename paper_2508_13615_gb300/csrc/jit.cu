@@ -1,0 +1,905 @@
+// Segment compiler: a fused segment's register-tile program, compiled into a
+// straight-line kernel.
+//
+// The register-tile interpreter (fused_reg.cu) reads each op of a segment at
+// run time: its kind, its register slot, its control pattern and its
+// coefficient offsets, and for every amplitude it tests predicates against
+// layout tables.  On GB300 that dispatch costs more issue slots than the
+// gate arithmetic itself.  Here the same program is written out as CUDA C++
+// in which all of that is constant: the register element of every pair, which
+// elements a register-held control selects, the thread part of each layout
+// (a handful of shifts once per exchange), and the parameter-space offset of
+// each coefficient.  Uncontrolled X/CNOT-type swaps become renamings of
+// register variables.  The coefficients stay kernel parameters, so circuits
+// that differ only in their angles share one compiled kernel.
+//
+// The source is compiled for sm_103a by NVRTC (loaded with dlopen, so the
+// library has no link-time dependency on it) and loaded through the driver
+// API (entry points obtained from the runtime), once per structure and
+// device; kernels are cached for the life of the process.
+#include <dlfcn.h>
+#include <cuda.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "arith.cuh"
+#include "jit.h"
+#include "lqs_internal.cuh"
+#include "tile.cuh"
+
+#include "jit_headers.inc"  // kJitHeaderNames / kJitHeaderSources (written by the build)
+
+namespace lqs {
+
+// ---------------------------------------------------------------------------
+// source generation
+// ---------------------------------------------------------------------------
+namespace {
+
+uint32_t host_swz(uint32_t j, int sz) {
+  if (sz == 16) return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7u);
+  return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
+}
+
+std::string hex(uint64_t x) {
+  char b[32];
+  std::snprintf(b, sizeof b, "0x%llxull", (unsigned long long)x);
+  return b;
+}
+std::string hex32(uint32_t x) {
+  char b[24];
+  std::snprintf(b, sizeof b, "0x%xu", x);
+  return b;
+}
+
+class SegGen {
+ public:
+  SegGen(int k, int r, const char* aname, int amp_bytes) : k_(k), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes) {}
+
+  // Returns false (with a reason) for a program this generator does not take.
+  bool run(const TOp* ops, int nops, int ncoef, std::string& src, std::string& kname, std::string& why);
+
+ private:
+  int k_, r_, R_;
+  const char* aname_;
+  int sz_;
+  int slot_[4] = {0, 0, 0, 0};  // register slot m -> local position
+  int thr_[16] = {0};           // thread bit m -> local position
+  int vm_[16];                  // register element -> variable
+  int uid_ = 0;
+  std::ostringstream o_;    // tile-loop body
+  std::ostringstream pre_;  // before the tile loop (tile-independent per-thread values)
+  std::string why_;
+
+  bool set_layout(uint64_t packed);
+  uint32_t je(int e) const {
+    uint32_t x = 0;
+    for (int m = 0; m < r_; ++m)
+      if ((e >> m) & 1) x |= 1u << slot_[m];
+    return x;
+  }
+  int reg_slot(int pos) const {
+    for (int m = 0; m < r_; ++m)
+      if (slot_[m] == pos) return m;
+    return -1;
+  }
+  uint32_t reg_positions() const {
+    uint32_t x = 0;
+    for (int m = 0; m < r_; ++m) x |= 1u << slot_[m];
+    return x;
+  }
+  std::string jt_expr() const;
+  std::string V(int e) const { return "v" + std::to_string(vm_[e]); }
+  std::string cref(int i) const { return "P.coef[" + std::to_string(i) + "]"; }
+  std::string fresh(const char* p) { return std::string(p) + std::to_string(uid_++); }
+  // predicate of the op's thread-held and outside controls ("" when none),
+  // and the register-slot mask its register-held controls require
+  std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
+  bool emit_op(const TOp& t);
+  void emit_layout(const TOp& t);
+  bool fail(const std::string& w) {
+    why_ = w;
+    return false;
+  }
+};
+
+bool SegGen::set_layout(uint64_t packed) {
+  uint32_t seen = 0;
+  for (int i = 0; i < k_; ++i) {
+    const int p = (int)((packed >> (4 * i)) & 15u);
+    if (p >= k_ || ((seen >> p) & 1u)) return false;  // not a permutation of the tile bits
+    seen |= 1u << p;
+    if (i < r_) slot_[i] = p;
+    else thr_[i - r_] = p;
+  }
+  return true;
+}
+
+std::string SegGen::jt_expr() const {
+  const int tb = k_ - r_;
+  std::string s;
+  for (int m = 0; m < tb;) {
+    int len = 1;
+    while (m + len < tb && thr_[m + len] == thr_[m] + len) ++len;
+    const uint32_t mask = (1u << len) - 1u;
+    std::string term = m ? "(tid >> " + std::to_string(m) + ")" : std::string("tid");
+    if (m + len < 32 && !(m == 0 && len == tb)) term = "(" + term + " & " + hex32(mask) + ")";
+    if (thr_[m]) term = "(" + term + " << " + std::to_string(thr_[m]) + ")";
+    s += s.empty() ? term : " | " + term;
+    m += len;
+  }
+  return s.empty() ? std::string("0u") : s;
+}
+
+std::string SegGen::pred(uint32_t lc, uint64_t ec, uint32_t& regc) const {
+  regc = 0;
+  uint32_t thc = 0;
+  for (int p = 0; p < k_; ++p) {
+    if (!((lc >> p) & 1u)) continue;
+    const int m = reg_slot(p);
+    if (m >= 0) regc |= 1u << m;
+    else thc |= 1u << p;
+  }
+  std::string s;
+  if (thc) s = "((jt & " + hex32(thc) + ") == " + hex32(thc) + ")";
+  if (ec) s += std::string(s.empty() ? "" : " && ") + "((base & " + hex(ec) + ") == " + hex(ec) + ")";
+  return s;
+}
+
+void SegGen::emit_layout(const TOp& t) {
+  // write the tile in the current layout, read it back in the new one
+  o_ << "    __syncthreads();\n    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+  for (int e = 0; e < R_; ++e)
+    o_ << "      lqs::st_w(&X1[sj ^ " << hex32(host_swz(je(e), sz_)) << "], " << V(e) << ");\n";
+  o_ << "    }\n    __syncthreads();\n";
+  set_layout(t.ecmask);  // validated by the caller
+  o_ << "    jt = " << jt_expr() << ";\n    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+  for (int e = 0; e < R_; ++e) {
+    vm_[e] = e;
+    o_ << "      v" << e << " = lqs::ld_w(&X1[sj ^ " << hex32(host_swz(je(e), sz_)) << "]);\n";
+  }
+  o_ << "    }\n";
+  if (t.e0 != t.ecmask) {  // relabelling SWAPs: from here on amplitudes carry their logical positions
+    set_layout(t.e0);
+    o_ << "    jt = " << jt_expr() << ";\n";
+  }
+}
+
+bool SegGen::emit_op(const TOp& t) {
+  uint32_t regc = 0;
+  const int c = t.coef;
+  auto qual = [&](int e) { return ((uint32_t)e & regc) == regc; };
+  switch (t.kind) {
+    case K_LAYOUT:
+      return fail("internal: layout reached emit_op");
+    case K_PHASE: {
+      const std::string p = pred(t.lcmask, t.ecmask, regc);
+      o_ << "    // phase\n";
+      if (!p.empty()) o_ << "    if (" << p << ") {\n";
+      for (int e = 0; e < R_; ++e) {
+        if (!qual(e)) continue;
+        const std::string v = V(e);
+        switch (t.special) {
+          case 1: o_ << "      " << v << " = A::neg(" << v << ");\n"; break;
+          case 2: o_ << "      " << v << " = A::mul_i(" << v << ");\n"; break;
+          case 3: o_ << "      " << v << " = A::neg(A::mul_i(" << v << "));\n"; break;
+          default: o_ << "      " << v << " = A::cmul(" << cref(c) << ", " << v << ");\n"; break;
+        }
+      }
+      if (!p.empty()) o_ << "    }\n";
+      return true;
+    }
+    case K_DIAG1: {
+      const std::string p = pred(t.lcmask, t.ecmask, regc);
+      o_ << "    // diagonal\n";
+      if (!p.empty()) o_ << "    if (" << p << ") {\n";
+      const int m = t.l0 >= 0 ? reg_slot(t.l0) : -1;
+      if (m >= 0) {
+        for (int e = 0; e < R_; ++e)
+          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << cref(c + ((e >> m) & 1)) << ", " << V(e) << ");\n";
+      } else {
+        const std::string d = fresh("d");
+        const std::string bit = t.l0 >= 0 ? "((jt >> " + std::to_string(t.l0) + ") & 1u)"
+                                          : "((base & " + hex(t.e0) + ") != 0ull)";
+        o_ << "      const C " << d << " = " << bit << " ? " << cref(c + 1) << " : " << cref(c) << ";\n";
+        for (int e = 0; e < R_; ++e)
+          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << d << ", " << V(e) << ");\n";
+      }
+      if (!p.empty()) o_ << "    }\n";
+      return true;
+    }
+    case K_DIAG2: {
+      const std::string p = pred(t.lcmask, t.ecmask, regc);
+      o_ << "    // two-qubit diagonal\n";
+      if (!p.empty()) o_ << "    if (" << p << ") {\n";
+      // each target bit: a register slot (known per element) or a runtime bit
+      const int m0 = t.l0 >= 0 ? reg_slot(t.l0) : -1, m1 = t.l1 >= 0 ? reg_slot(t.l1) : -1;
+      auto rbit = [&](int l, uint64_t em) {
+        return l >= 0 ? "((jt >> " + std::to_string(l) + ") & 1u)" : "((base & " + hex(em) + ") != 0ull)";
+      };
+      const std::string r0 = rbit(t.l0, t.e0), r1 = rbit(t.l1, t.e1);
+      std::map<int, std::string> sel;  // compile-time pattern -> coefficient expression
+      for (int e = 0; e < R_; ++e) {
+        if (!qual(e)) continue;
+        const int b0 = m0 >= 0 ? (e >> m0) & 1 : -1, b1 = m1 >= 0 ? (e >> m1) & 1 : -1;
+        std::string f;
+        if (b0 >= 0 && b1 >= 0) {
+          f = cref(c + 2 * b0 + b1);
+        } else {
+          const int key = (b0 + 1) * 3 + (b1 + 1);
+          auto it = sel.find(key);
+          if (it == sel.end()) {
+            std::string ex;
+            if (b0 < 0 && b1 >= 0) ex = r0 + " ? " + cref(c + 2 + b1) + " : " + cref(c + b1);
+            else if (b0 >= 0 && b1 < 0) ex = r1 + " ? " + cref(c + 2 * b0 + 1) + " : " + cref(c + 2 * b0);
+            else
+              ex = r0 + " ? (" + r1 + " ? " + cref(c + 3) + " : " + cref(c + 2) + ") : (" + r1 + " ? " + cref(c + 1) +
+                   " : " + cref(c) + ")";
+            const std::string d = fresh("d");
+            o_ << "      const C " << d << " = " << ex << ";\n";
+            it = sel.emplace(key, d).first;
+          }
+          f = it->second;
+        }
+        o_ << "      " << V(e) << " = A::cmul(" << f << ", " << V(e) << ");\n";
+      }
+      if (!p.empty()) o_ << "    }\n";
+      return true;
+    }
+    case K_ANTI1:
+    case K_DENSE1:
+    case K_DENSE1R: {
+      const int m = t.l0 >= 0 ? reg_slot(t.l0) : -1;
+      if (m < 0) return fail("single-target op whose target is not in a register slot");
+      const std::string p = pred(t.lcmask, t.ecmask, regc);
+      if ((regc >> m) & 1u) return fail("control on the target slot");
+      const bool plain = t.kind == K_ANTI1 && t.special == 1;
+      o_ << "    // " << (t.kind == K_ANTI1 ? "anti-diagonal" : t.kind == K_DENSE1 ? "dense" : "real dense")
+         << " on slot " << m << "\n";
+      if (plain && p.empty()) {  // a register renaming: no code
+        for (int e = 0; e < R_; ++e)
+          if (!((e >> m) & 1) && qual(e)) std::swap(vm_[e], vm_[e | (1 << m)]);
+        return true;
+      }
+      if (plain) {
+        const std::string q = fresh("p");
+        o_ << "    { const bool " << q << " = " << p << ";\n";
+        for (int e = 0; e < R_; ++e)
+          if (!((e >> m) & 1) && qual(e))
+            o_ << "      lqs::jit::swap_if(" << q << ", " << V(e) << ", " << V(e | (1 << m)) << ");\n";
+        o_ << "    }\n";
+        return true;
+      }
+      if (t.kind == K_ANTI1 && p.empty()) {  // (a, b) <- (f0 b, f1 a): scale in place, then rename
+        for (int e = 0; e < R_; ++e) {
+          if ((e >> m) & 1 || !qual(e)) continue;
+          const int a = e, b = e | (1 << m);
+          o_ << "    " << V(b) << " = A::cmul(" << cref(c) << ", " << V(b) << ");\n";
+          o_ << "    " << V(a) << " = A::cmul(" << cref(c + 1) << ", " << V(a) << ");\n";
+          std::swap(vm_[a], vm_[b]);
+        }
+        return true;
+      }
+      if (!p.empty()) o_ << "    if (" << p << ") {\n";
+      for (int e = 0; e < R_; ++e) {
+        if ((e >> m) & 1 || !qual(e)) continue;
+        const std::string a = V(e), b = V(e | (1 << m));
+        if (t.kind == K_ANTI1)
+          o_ << "      lqs::jit::anti<A>(" << a << ", " << b << ", " << cref(c) << ", " << cref(c + 1) << ");\n";
+        else
+          o_ << "      lqs::jit::" << (t.kind == K_DENSE1 ? "d1" : "d1r") << "<A>(" << a << ", " << b << ", "
+             << cref(c) << ", " << cref(c + 1) << ", " << cref(c + 2) << ", " << cref(c + 3) << ");\n";
+      }
+      if (!p.empty()) o_ << "    }\n";
+      return true;
+    }
+    case K_SWAP:
+    case K_DENSE2: {
+      const int ma = t.l0 >= 0 ? reg_slot(t.l0) : -1, mb = t.l1 >= 0 ? reg_slot(t.l1) : -1;
+      if (ma < 0 || mb < 0 || ma == mb) return fail("two-target op whose targets are not in register slots");
+      const std::string p = pred(t.lcmask, t.ecmask, regc);
+      if ((regc >> ma) & 1u || (regc >> mb) & 1u) return fail("control on a target slot");
+      const int A_ = 1 << ma, B_ = 1 << mb;
+      o_ << "    // " << (t.kind == K_SWAP ? "controlled swap" : "dense 4x4") << " on slots " << ma << ", " << mb
+         << "\n";
+      if (t.kind == K_SWAP) {
+        if (p.empty()) {
+          for (int e = 0; e < R_; ++e)
+            if (!(e & A_) && !(e & B_) && qual(e)) std::swap(vm_[e | A_], vm_[e | B_]);
+          return true;
+        }
+        const std::string q = fresh("p");
+        o_ << "    { const bool " << q << " = " << p << ";\n";
+        for (int e = 0; e < R_; ++e)
+          if (!(e & A_) && !(e & B_) && qual(e))
+            o_ << "      lqs::jit::swap_if(" << q << ", " << V(e | A_) << ", " << V(e | B_) << ");\n";
+        o_ << "    }\n";
+        return true;
+      }
+      if (!p.empty()) o_ << "    if (" << p << ") {\n";
+      for (int e = 0; e < R_; ++e) {
+        if ((e & A_) || (e & B_) || !qual(e)) continue;
+        // amplitude order 2 * bit(t0) + bit(t1)
+        o_ << "      lqs::jit::d2<A>(" << V(e) << ", " << V(e | B_) << ", " << V(e | A_) << ", " << V(e | A_ | B_)
+           << ", &" << cref(c) << ");\n";
+      }
+      if (!p.empty()) o_ << "    }\n";
+      return true;
+    }
+    case K_DPROD: {
+      // C * prod of f_q over factor qubits q set in the amplitude's index, on
+      // amplitudes whose condition bits are all 1.  Pool: C, then the local
+      // factors by increasing tile position, then the outside factors by qubit.
+      const std::string p = pred(t.lcmask, t.ecmask, regc);
+      const uint32_t LF = (uint32_t)t.e1;
+      const uint64_t EF = t.e0;
+      auto lidx = [&](int q) { return c + 1 + __builtin_popcount(LF & ((1u << q) - 1u)); };
+      o_ << "    // merged diagonal run\n";
+      if (!p.empty()) o_ << "    if (" << p << ") {\n";
+      o_ << "    {\n";
+      // C times the factors on this thread's bits: the same for every tile,
+      // so it is formed once per thread before the tile loop
+      const uint32_t regpos = reg_positions();
+      std::string h = cref(c);
+      if (LF & ~regpos) {
+        h = fresh("h");
+        pre_ << "  C " << h << " = " << cref(c) << ";\n  { const uint32_t jt = " << jt_expr() << ";\n";
+        for (int q = 0; q < k_; ++q)
+          if (((LF >> q) & 1u) && !((regpos >> q) & 1u))
+            pre_ << "    if ((jt >> " << q << ") & 1u) " << h << " = A::kmul(" << cref(lidx(q)) << ", " << h << ");\n";
+        pre_ << "  }\n";
+      }
+      const std::string a = fresh("a");
+      o_ << "      C " << a << " = " << h << ";\n";
+      int j = 0;
+      for (int q = 0; q < 64; ++q) {
+        if (!((EF >> q) & 1ull)) continue;
+        o_ << "      if ((base >> " << q << ") & 1ull) " << a << " = A::kmul("
+           << cref(c + 1 + __builtin_popcount(LF) + j) << ", " << a << ");\n";
+        ++j;
+      }
+      uint32_t fmask = 0;  // register slots carrying a factor
+      for (int m = 0; m < r_; ++m)
+        if ((LF >> slot_[m]) & 1u) fmask |= 1u << m;
+      std::map<uint32_t, std::string> tab;
+      tab[0] = a;
+      // products for the needed factor patterns, each from a smaller one
+      std::vector<uint32_t> need;
+      for (int e = 0; e < R_; ++e)
+        if (qual(e)) need.push_back((uint32_t)e & fmask);
+      std::sort(need.begin(), need.end());
+      need.erase(std::unique(need.begin(), need.end()), need.end());
+      std::vector<uint32_t> all;
+      for (uint32_t key : need)
+        for (uint32_t x = key; x; x &= ~(1u << (31 - __builtin_clz(x)))) all.push_back(x);
+      std::sort(all.begin(), all.end());
+      all.erase(std::unique(all.begin(), all.end()), all.end());
+      for (uint32_t key : all) {
+        const int m = 31 - __builtin_clz(key);
+        const std::string nm = fresh("f");
+        o_ << "      const C " << nm << " = A::kmul(" << cref(lidx(slot_[m])) << ", " << tab[key ^ (1u << m)] << ");\n";
+        tab[key] = nm;
+      }
+      for (int e = 0; e < R_; ++e)
+        if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << tab[(uint32_t)e & fmask] << ", " << V(e) << ");\n";
+      o_ << "    }\n";
+      if (!p.empty()) o_ << "    }\n";
+      return true;
+    }
+    default:
+      return fail("op kind " + std::to_string((int)t.kind) + " has no compiled form");
+  }
+}
+
+const char* kSkeletonHead = R"(
+extern "C" __global__ void __launch_bounds__(256, 2)
+@NAME@(A::S* __restrict__ psi, const __grid_constant__ SegArgs P, int* status) {
+  typedef A::S S;
+  typedef A::W W;
+  typedef A::C C;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const lqs::TileGeom& G = P.g;
+  S* S0 = reinterpret_cast<S*>(smem_raw);
+  S* S1 = S0 + @NT@;
+  W* X1 = reinterpret_cast<W*>(S1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(S1 + @NT@);
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) {
+    lqs::mbar_init(bar, 1);
+    lqs::fence_mbar_init();
+  }
+  __syncthreads();
+  uint64_t t = blockIdx.x;
+  if (t < G.ntiles && tid < 32) lqs::tile_load_issue(G, S0, psi, lqs::tile_base(G, t), bar);
+  uint32_t phase = 0;
+  bool ok = true;
+@PRE@  for (; t < G.ntiles; t += gridDim.x) {
+    const uint64_t base = lqs::tile_base(G, t);
+    ok = __syncthreads_and(lqs::mbar_wait(bar, phase));
+    phase ^= 1u;
+    if (!ok) break;
+)";
+
+const char* kSkeletonTail = R"(    lqs::fence_proxy_async();
+    __syncthreads();
+    if (tid < 32) lqs::tile_store_issue(G, psi, S1, base);
+  }
+  if (tid < 32) lqs::bulk_wait0();
+  if (!ok && tid == 0) {
+    lqs::flag_timeout(status, 4);
+    lqs::mbar_wait(bar, phase ^ 1u);
+  }
+}
+)";
+
+std::string replace_all(std::string s, const std::string& a, const std::string& b) {
+  for (size_t p = s.find(a); p != std::string::npos; p = s.find(a, p + b.size())) s.replace(p, a.size(), b);
+  return s;
+}
+
+uint64_t fnv1a(const std::string& s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char ch : s) {
+    h ^= ch;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::string& kname, std::string& why) {
+  if (nops < 1 || ops[0].kind != K_LAYOUT) {
+    why = "program does not start with a layout";
+    return false;
+  }
+  for (int i = 0; i < nops; ++i)
+    if (ops[i].kind == K_LAYOUT) {
+      if (!set_layout(ops[i].ecmask) || !set_layout(ops[i].e0)) {
+        why = "layout is not a permutation of the tile bits";
+        return false;
+      }
+    }
+  // the first layout loads the incoming tile
+  set_layout(ops[0].ecmask);
+  for (int e = 0; e < R_; ++e) vm_[e] = e;
+  o_ << "    uint32_t jt = " << jt_expr() << ";\n";
+  o_ << "    W";
+  for (int e = 0; e < R_; ++e) o_ << (e ? ", v" : " v") << e;
+  o_ << ";\n";
+  for (int e = 0; e < R_; ++e) o_ << "    v" << e << " = A::load(S0[jt + " << hex32(je(e)) << "]);\n";
+  if (ops[0].e0 != ops[0].ecmask) {
+    set_layout(ops[0].e0);
+    o_ << "    jt = " << jt_expr() << ";\n";
+  }
+  o_ << "    __syncthreads();  // the incoming buffer is free: prefetch the next tile into it\n"
+        "    { const uint64_t tn = t + gridDim.x;\n"
+        "      if (tn < G.ntiles && tid < 32) lqs::tile_load_issue(G, S0, psi, lqs::tile_base(G, tn), bar); }\n";
+  for (int i = 1; i < nops; ++i) {
+    if (ops[i].kind == K_LAYOUT) {
+      emit_layout(ops[i]);
+      continue;
+    }
+    if (!emit_op(ops[i])) {
+      why = why_;
+      return false;
+    }
+  }
+  o_ << "    __syncthreads();  // exchange readers are done before the result overwrites the buffer\n";
+  for (int e = 0; e < R_; ++e) o_ << "    S1[jt + " << hex32(je(e)) << "] = A::store(" << V(e) << ");\n";
+  const std::string body = o_.str();
+  const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^ fnv1a(aname_);
+  char nm[40];
+  std::snprintf(nm, sizeof nm, "lqs_seg_%016llx", (unsigned long long)h);
+  kname = nm;
+  std::ostringstream s;
+  s << "// compiled fused segment: " << nops << " ops, " << ncoef << " coefficients\n"
+    << "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
+       "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n"
+    << "#include \"tile.cuh\"\n#include \"jit_dev.cuh\"\n"
+    << "typedef " << aname_ << " A;\n"
+    << "struct SegArgs {\n  lqs::TileGeom g;\n  A::C coef[" << std::max(ncoef, 1) << "];\n};\n";
+  std::string head = replace_all(kSkeletonHead, "@NAME@", kname);
+  head = replace_all(head, "@NT@", std::to_string(1u << k_) + "u");
+  head = replace_all(head, "@PRE@", pre_.str());
+  s << head << body << kSkeletonTail;
+  src = s.str();
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// NVRTC and driver entry points (resolved at first use)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Nvrtc {
+  bool tried = false, ok = false;
+  std::string err;
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) get_log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) get_cubin = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  decltype(&nvrtcGetErrorString) errstr = nullptr;
+};
+
+struct Driver {
+  bool tried = false, ok = false;
+  std::string err;
+  decltype(&cuModuleLoadData) load = nullptr;
+  decltype(&cuModuleGetFunction) get_function = nullptr;
+  decltype(&cuFuncSetAttribute) set_attr = nullptr;
+  decltype(&cuFuncGetAttribute) get_attr = nullptr;
+  decltype(&cuLaunchKernel) launch = nullptr;
+  decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) occupancy = nullptr;
+  decltype(&cuGetErrorString) errstr = nullptr;
+};
+
+std::mutex g_load_mu;
+Nvrtc g_nvrtc;
+Driver g_drv;
+
+bool load_nvrtc() {
+  std::lock_guard<std::mutex> lk(g_load_mu);
+  Nvrtc& N = g_nvrtc;
+  if (N.tried) return N.ok;
+  N.tried = true;
+  std::vector<std::string> cands;
+  if (const char* p = std::getenv("LQS_NVRTC")) cands.push_back(p);
+  cands.push_back("libnvrtc.so.13");
+  cands.push_back("libnvrtc.so");
+  for (const char* env : {"CUDA_HOME", "CUDA_PATH"})
+    if (const char* p = std::getenv(env)) cands.push_back(std::string(p) + "/lib64/libnvrtc.so.13");
+  cands.push_back("/usr/local/cuda/lib64/libnvrtc.so.13");
+  void* h = nullptr;
+  for (const auto& c : cands)
+    if ((h = dlopen(c.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
+  if (!h) {
+    N.err = "libnvrtc.so.13 not found (set LQS_NVRTC to its path)";
+    return false;
+  }
+#define LQS_SYM(field, name)                                          \
+  N.field = reinterpret_cast<decltype(N.field)>(dlsym(h, name));       \
+  if (!N.field) {                                                      \
+    N.err = std::string("libnvrtc lacks ") + name;                     \
+    return false;                                                      \
+  }
+  LQS_SYM(create, "nvrtcCreateProgram")
+  LQS_SYM(compile, "nvrtcCompileProgram")
+  LQS_SYM(log_size, "nvrtcGetProgramLogSize")
+  LQS_SYM(get_log, "nvrtcGetProgramLog")
+  LQS_SYM(cubin_size, "nvrtcGetCUBINSize")
+  LQS_SYM(get_cubin, "nvrtcGetCUBIN")
+  LQS_SYM(destroy, "nvrtcDestroyProgram")
+  LQS_SYM(errstr, "nvrtcGetErrorString")
+#undef LQS_SYM
+  N.ok = true;
+  return true;
+}
+
+bool load_driver() {
+  std::lock_guard<std::mutex> lk(g_load_mu);
+  Driver& D = g_drv;
+  if (D.tried) return D.ok;
+  D.tried = true;
+  auto get = [&](const char* name, void** fn) {
+    cudaDriverEntryPointQueryResult q{};
+    const cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !*fn) {
+      D.err = std::string("driver entry point ") + name + " unavailable";
+      return false;
+    }
+    return true;
+  };
+  D.ok = get("cuModuleLoadData", reinterpret_cast<void**>(&D.load)) &&
+         get("cuModuleGetFunction", reinterpret_cast<void**>(&D.get_function)) &&
+         get("cuFuncSetAttribute", reinterpret_cast<void**>(&D.set_attr)) &&
+         get("cuFuncGetAttribute", reinterpret_cast<void**>(&D.get_attr)) &&
+         get("cuLaunchKernel", reinterpret_cast<void**>(&D.launch)) &&
+         get("cuOccupancyMaxActiveBlocksPerMultiprocessor", reinterpret_cast<void**>(&D.occupancy)) &&
+         get("cuGetErrorString", reinterpret_cast<void**>(&D.errstr));
+  return D.ok;
+}
+
+int cu_error(CUresult r, const char* what) {
+  const char* s = nullptr;
+  if (g_drv.errstr) g_drv.errstr(r, &s);
+  return set_error(LQS_ERR_CUDA, std::string(what) + ": " + (s ? s : "CUDA driver error") + " (" +
+                                     std::to_string((int)r) + ")");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// cache
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kJitMaxDevices = 64;
+constexpr size_t kJitMaxEntries = 4096;
+constexpr int kJitAutoMinQubits = 20;
+
+struct Entry {
+  std::string src, name;
+  int uses = 0;
+  int state = 0;  // 0 not compiled, 1 compiled, 2 failed
+  std::vector<char> cubin;
+  std::string log;
+  CUfunction fn[kJitMaxDevices] = {};
+  int per_sm[kJitMaxDevices] = {};
+};
+
+std::mutex g_mu;
+std::unordered_map<std::string, std::unique_ptr<Entry>> g_cache;
+std::atomic<int> g_mode{-1};
+std::atomic<int> g_compiled{0}, g_failed{0};
+std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_compile_us{0};
+std::string g_last_jit_error;
+
+int mode_now() {
+  int m = g_mode.load();
+  if (m < 0) {
+    m = LQS_JIT_AUTO;
+    if (const char* e = std::getenv("LQS_JIT")) {
+      const int v = std::atoi(e);
+      if (v == LQS_JIT_OFF || v == LQS_JIT_ON || v == LQS_JIT_AUTO) m = v;
+    }
+    int expect = -1;
+    g_mode.compare_exchange_strong(expect, m);
+    m = g_mode.load();
+  }
+  return m;
+}
+
+bool wants_compile(const Entry& e, int n) {
+  const int m = mode_now();
+  if (m == LQS_JIT_ON) return true;
+  if (m == LQS_JIT_AUTO) return n >= kJitAutoMinQubits && e.uses >= 2;
+  return false;
+}
+
+// Compiles one entry (no lock held: NVRTC programs are independent).
+void compile_entry(Entry* e) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (const char* dir = std::getenv("LQS_JIT_DUMP")) {  // keep the generated source for inspection
+    if (FILE* f = std::fopen((std::string(dir) + "/" + e->name + ".cu").c_str(), "w")) {
+      std::fwrite(e->src.data(), 1, e->src.size(), f);
+      std::fclose(f);
+    }
+  }
+  Nvrtc& N = g_nvrtc;
+  nvrtcProgram prog = nullptr;
+  std::string log;
+  std::vector<char> cubin;
+  bool ok = false;
+  if (N.create(&prog, e->src.c_str(), (e->name + ".cu").c_str(), kJitHeaderCount, kJitHeaderSources,
+               kJitHeaderNames) == NVRTC_SUCCESS) {
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
+    const nvrtcResult r = N.compile(prog, 4, opts);
+    size_t ls = 0;
+    if (N.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
+      log.resize(ls);
+      N.get_log(prog, &log[0]);
+    }
+    size_t cs = 0;
+    if (r == NVRTC_SUCCESS && N.cubin_size(prog, &cs) == NVRTC_SUCCESS && cs) {
+      cubin.resize(cs);
+      ok = N.get_cubin(prog, cubin.data()) == NVRTC_SUCCESS;
+    } else if (r != NVRTC_SUCCESS && log.empty()) {
+      log = N.errstr(r);
+    }
+    N.destroy(&prog);
+  } else {
+    log = "nvrtcCreateProgram failed";
+  }
+  const auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+  g_compile_us += (uint64_t)us;
+  std::lock_guard<std::mutex> lk(g_mu);
+  e->cubin = std::move(cubin);
+  e->log = std::move(log);
+  e->state = ok ? 1 : 2;
+  if (ok) ++g_compiled;
+  else {
+    ++g_failed;
+    g_last_jit_error = e->name + ": " + e->log.substr(0, 400);
+  }
+}
+
+// Compiles entries on up to 8 threads.
+void compile_all(const std::vector<Entry*>& todo) {
+  if (todo.empty()) return;
+  const size_t nt = std::min<size_t>(todo.size(), std::max(1u, std::min(8u, std::thread::hardware_concurrency())));
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    for (size_t i; (i = next.fetch_add(1)) < todo.size();) compile_entry(todo[i]);
+  };
+  std::vector<std::thread> th;
+  for (size_t i = 1; i < nt; ++i) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+}
+
+Entry* find_or_add(const std::string& src, const std::string& name, bool count_use) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_cache.find(src);
+  if (it == g_cache.end()) {
+    if (g_cache.size() >= kJitMaxEntries) return nullptr;
+    auto e = std::make_unique<Entry>();
+    e->src = src;
+    e->name = name;
+    it = g_cache.emplace(src, std::move(e)).first;
+  }
+  if (count_use) ++it->second->uses;
+  return it->second.get();
+}
+
+}  // namespace
+
+template <class A> struct JitTypeName;
+template <> struct JitTypeName<ArF32> { static constexpr const char* s = "lqs::ArF32"; };
+template <> struct JitTypeName<ArF64> { static constexpr const char* s = "lqs::ArF64"; };
+template <> struct JitTypeName<ArDF> { static constexpr const char* s = "lqs::ArDF"; };
+
+template <class A>
+int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why) {
+  SegGen g(P.g.k, r, JitTypeName<A>::s, A::kAmpBytes);
+  return g.run(P.op, P.nops, P.ncoef, src, name, why) ? LQS_OK : LQS_ERR_UNSUPPORTED;
+}
+
+int jit_mode() { return mode_now(); }
+
+bool jit_enabled_for(int n) {
+  const int m = mode_now();
+  return m == LQS_JIT_ON || (m == LQS_JIT_AUTO && n >= kJitAutoMinQubits);
+}
+
+template <class A>
+int jit_note(const TileProg<A>& P, int r, int n, bool force, std::vector<void*>& todo) {
+  std::string src, name, why;
+  if (jit_source(P, r, src, name, why) != LQS_OK) return LQS_OK;  // the interpreter runs it
+  Entry* e = find_or_add(src, name, true);
+  if (!e) return LQS_OK;
+  if (e->state == 0 && (force || wants_compile(*e, n)) &&
+      std::find(todo.begin(), todo.end(), (void*)e) == todo.end())
+    todo.push_back(e);
+  return LQS_OK;
+}
+
+int jit_compile(const std::vector<void*>& todo) {
+  if (todo.empty()) return LQS_OK;
+  if (!load_nvrtc()) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_last_jit_error = g_nvrtc.err;
+    return set_error(LQS_ERR_UNSUPPORTED, g_nvrtc.err);
+  }
+  std::vector<Entry*> es;
+  for (void* p : todo) es.push_back(static_cast<Entry*>(p));
+  compile_all(es);
+  return LQS_OK;
+}
+
+int jit_states(const std::vector<void*>& todo, int* ok, std::string* err) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int good = 0;
+  bool bad = false;
+  for (void* p : todo) {
+    const Entry* e = static_cast<const Entry*>(p);
+    if (e->state == 1) {
+      ++good;
+    } else if (!bad) {
+      bad = true;
+      if (err) *err = e->name + ": " + e->log.substr(0, 2000);
+    }
+  }
+  if (ok) *ok = good;
+  return bad ? LQS_ERR_UNSUPPORTED : LQS_OK;
+}
+
+template <class A>
+int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, const char* prof_name,
+               bool* launched) {
+  *launched = false;
+  if (!jit_enabled_for(sv->n)) return LQS_OK;
+  std::string src, name, why;
+  if (jit_source(P, r, src, name, why) != LQS_OK) return LQS_OK;
+  Entry* e = find_or_add(src, name, false);
+  if (!e || e->state != 1) return LQS_OK;
+  const int dev = sv->device;
+  if (dev < 0 || dev >= kJitMaxDevices) return LQS_OK;
+  const size_t smem = 2 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;
+  CUfunction fn;
+  int per_sm;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!e->fn[dev]) {
+      if (!load_driver()) return set_error(LQS_ERR_UNSUPPORTED, g_drv.err);
+      LQS_CUDA_TRY(cudaSetDevice(dev));  // makes the device's primary context current on this thread
+      CUmodule mod;
+      CUresult rr = g_drv.load(&mod, e->cubin.data());
+      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuModuleLoadData(compiled segment)");
+      CUfunction f;
+      rr = g_drv.get_function(&f, mod, e->name.c_str());
+      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuModuleGetFunction(compiled segment)");
+      rr = g_drv.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem);
+      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuFuncSetAttribute(compiled segment)");
+      int ps = 0;
+      rr = g_drv.occupancy(&ps, f, kTileThreads, smem);
+      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+      e->per_sm[dev] = std::max(ps, 1);
+      e->fn[dev] = f;
+    }
+    fn = e->fn[dev];
+    per_sm = e->per_sm[dev];
+  }
+  // kernel parameters: the tile geometry, then the used coefficients
+  using C = typename A::C;
+  const size_t off = (sizeof(TileGeom) + alignof(C) - 1) / alignof(C) * alignof(C);
+  const size_t nc = (size_t)std::max(P.ncoef, 1);
+  std::vector<unsigned char> args((off + nc * sizeof(C) + 15) / 16 * 16, 0);
+  std::memcpy(args.data(), &P.g, sizeof(TileGeom));
+  std::memcpy(args.data() + off, P.coef, (size_t)P.ncoef * sizeof(C));
+  void* psi = sv->d;
+  int* status = sv->d_status;
+  void* kp[] = {&psi, args.data(), &status};
+  const uint64_t grid = std::min<uint64_t>(P.g.ntiles, (uint64_t)std::max(sv->sms, 1) * per_sm);
+  ProfScope ps(sv->stream, prof_name, bytes, flops);
+  const CUresult rr = g_drv.launch(fn, (unsigned)grid, 1, 1, kTileThreads, 1, 1, (unsigned)smem,
+                                   (CUstream)sv->stream, kp, nullptr);
+  if (rr != CUDA_SUCCESS) return cu_error(rr, "cuLaunchKernel(compiled segment)");
+  count_launch();
+  ++g_launches;
+  *launched = true;
+  return LQS_OK;
+}
+
+template int jit_source<ArF32>(const TileProg<ArF32>&, int, std::string&, std::string&, std::string&);
+template int jit_source<ArF64>(const TileProg<ArF64>&, int, std::string&, std::string&, std::string&);
+template int jit_source<ArDF>(const TileProg<ArDF>&, int, std::string&, std::string&, std::string&);
+template int jit_note<ArF32>(const TileProg<ArF32>&, int, int, bool, std::vector<void*>&);
+template int jit_note<ArF64>(const TileProg<ArF64>&, int, int, bool, std::vector<void*>&);
+template int jit_note<ArDF>(const TileProg<ArDF>&, int, int, bool, std::vector<void*>&);
+template int jit_launch<ArF32>(const TileProg<ArF32>&, int, SV*, double, double, const char*, bool*);
+template int jit_launch<ArF64>(const TileProg<ArF64>&, int, SV*, double, double, const char*, bool*);
+template int jit_launch<ArDF>(const TileProg<ArDF>&, int, SV*, double, double, const char*, bool*);
+
+}  // namespace lqs
+
+using namespace lqs;
+
+extern "C" int lqs_set_jit(int mode) {
+  if (mode != LQS_JIT_OFF && mode != LQS_JIT_ON && mode != LQS_JIT_AUTO)
+    return set_error(LQS_ERR_ARG, "mode must be LQS_JIT_OFF, LQS_JIT_ON or LQS_JIT_AUTO");
+  g_mode.store(mode);
+  return LQS_OK;
+}
+
+extern "C" int lqs_jit_info(lqs_jit_stats* out) {
+  if (!out) return set_error(LQS_ERR_ARG, "out is NULL");
+  std::memset(out, 0, sizeof *out);
+  out->mode = mode_now();
+  out->compiled = g_compiled.load();
+  out->failed = g_failed.load();
+  out->launches = g_launches.load();
+  out->compile_seconds = (double)g_compile_us.load() * 1e-6;
+  std::lock_guard<std::mutex> lk(g_mu);
+  out->cached = (int)g_cache.size();
+  std::snprintf(out->last_error, sizeof out->last_error, "%s", g_last_jit_error.c_str());
+  return LQS_OK;
+}

@@ -1,0 +1,79 @@
+// Device helpers for runtime-compiled segment kernels.
+//
+// A compiled segment is straight-line code: every register index, layout,
+// control pattern and coefficient offset is a constant of its source, so the
+// kernel carries none of the register-tile interpreter's per-op dispatch.
+// The helpers here are the pair and quad updates it is written in; they use
+// the same arithmetic policies (arith.cuh) as every other kernel of the
+// library, so a compiled segment and the interpreter compute the same
+// products and sums.
+#pragma once
+#include "arith.cuh"
+
+namespace lqs {
+namespace jit {
+
+template <class A> struct Re;
+template <> struct Re<ArF32> { static __device__ __forceinline__ float get(const float2& c) { return c.x; } };
+template <> struct Re<ArF64> { static __device__ __forceinline__ double get(const double2& c) { return c.x; } };
+template <> struct Re<ArDF> { static __device__ __forceinline__ DF get(const DFK& c) { return c.re; } };
+
+// (a, b) <- (u00 a + u01 b, u10 a + u11 b)
+template <class A>
+__device__ __forceinline__ void d1(typename A::W& a, typename A::W& b, const typename A::C& u00,
+                                   const typename A::C& u01, const typename A::C& u10, const typename A::C& u11) {
+  const typename A::W x = a, y = b;
+  a = A::cmac2(u00, x, u01, y);
+  b = A::cmac2(u10, x, u11, y);
+}
+
+// the same with a real matrix (real parts of the coefficients)
+template <class A>
+__device__ __forceinline__ void d1r(typename A::W& a, typename A::W& b, const typename A::C& u00,
+                                    const typename A::C& u01, const typename A::C& u10, const typename A::C& u11) {
+  const typename A::W x = a, y = b;
+  a = A::rmac2(Re<A>::get(u00), x, Re<A>::get(u01), y);
+  b = A::rmac2(Re<A>::get(u10), x, Re<A>::get(u11), y);
+}
+
+// (x0..x3) <- U x with U row-major at u[0..15]
+template <class A>
+__device__ __forceinline__ void d2(typename A::W& x0, typename A::W& x1, typename A::W& x2, typename A::W& x3,
+                                   const typename A::C* u) {
+  const typename A::W x[4] = {x0, x1, x2, x3};
+  x0 = A::cmac4(u, x);
+  x1 = A::cmac4(u + 4, x);
+  x2 = A::cmac4(u + 8, x);
+  x3 = A::cmac4(u + 12, x);
+}
+
+// (a, b) <- (f0 b, f1 a)
+template <class A>
+__device__ __forceinline__ void anti(typename A::W& a, typename A::W& b, const typename A::C& f0,
+                                     const typename A::C& f1) {
+  const typename A::W x = a;
+  a = A::cmul(f0, b);
+  b = A::cmul(f1, x);
+}
+
+// exchange a and b where p holds (a per-thread predicate)
+template <class W>
+__device__ __forceinline__ void swap_if(bool p, W& a, W& b) {
+  const W x = a, y = b;
+  a = p ? y : x;
+  b = p ? x : y;
+}
+
+// Exchange-buffer position of a local amplitude index (same fold as the
+// interpreter's buffer, so bank spread is unchanged).  It is linear over XOR,
+// so for a thread part jt and a register part c with disjoint bits,
+// swz(jt | c) = swz(jt) ^ swz(c): the thread part is folded once per layout
+// and the register parts are constants.
+template <int SZ>
+__device__ __forceinline__ uint32_t swz(uint32_t j) {
+  if (SZ == 16) return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7u);
+  return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
+}
+
+}  // namespace jit
+}  // namespace lqs

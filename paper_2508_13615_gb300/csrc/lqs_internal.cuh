@@ -141,6 +141,13 @@ int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, cons
 // LQS_ERR_UNSUPPORTED when the segment's program does not fit (split it).
 int reg_tile_qubits(int dtype);
 int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith);
+// Segment compiler hooks: note_reg_prog builds a segment's register-tile
+// program (LQS_ERR_UNSUPPORTED when it must be split) and notes it;
+// jit_collect walks a segment the way launch_segment routes and splits it.
+int note_reg_prog(int n, int dtype, int arith, const std::vector<KOp>& ops, const Segment& seg, int k, int b,
+                  bool force, std::vector<void*>& todo);
+int jit_collect(int n, int dtype, int arith, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc,
+                bool force, std::vector<void*>& todo);
 
 // ---------------------------------------------------------------------------
 // reductions / expectation values / adjoint

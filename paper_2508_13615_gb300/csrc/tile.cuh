@@ -9,8 +9,10 @@
 // (Sec. 2, Fig. 1a); on one GPU the analogue of a process's local vector is a
 // tile held in shared memory.
 #pragma once
+#ifndef __CUDACC_RTC__  // runtime-compiled segment kernels bring their own integer types
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "arith.cuh"
 

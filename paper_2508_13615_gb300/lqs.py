@@ -25,6 +25,7 @@ LQS_ERR_UNSUPPORTED = -5
 LQS_C64 = 0
 LQS_C128 = 1
 LQS_ARITH_AUTO, LQS_ARITH_F64, LQS_ARITH_DF = 0, 1, 2
+LQS_JIT_OFF, LQS_JIT_ON, LQS_JIT_AUTO = 0, 1, 2
 
 #: gate ids of the ABI (lqs_gate), by the names used in circuit descriptions
 GATE_IDS = {
@@ -60,6 +61,12 @@ class lqs_batch_item(ctypes.Structure):
 class lqs_launch_record(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char * 48), ("ms", ctypes.c_float), ("bytes", ctypes.c_double),
                 ("flops", ctypes.c_double)]
+
+
+class lqs_jit_stats(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("compiled", ctypes.c_int), ("failed", ctypes.c_int),
+                ("cached", ctypes.c_int), ("launches", ctypes.c_uint64), ("compile_seconds", ctypes.c_double),
+                ("last_error", ctypes.c_char * 256)]
 
 
 class LqsError(RuntimeError):
@@ -102,6 +109,10 @@ def _load():
         "lqs_sv_distance": (i32, [vp, vp, dp, dp]),
         "lqs_profile_start": (i32, []),
         "lqs_profile_stop": (i32, [ctypes.POINTER(lqs_launch_record), i32, ip]),
+        "lqs_set_jit": (i32, [i32]),
+        "lqs_jit_info": (i32, [ctypes.POINTER(lqs_jit_stats)]),
+        "lqs_jit_precompile": (i32, [i32, i32, i32, ctypes.POINTER(lqs_op), i32, dp, i32,
+                                     ctypes.POINTER(lqs_fuse_cfg), ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -391,3 +402,28 @@ def lqs_sv_distance(ha, hb) -> Tuple[float, float]:
     d, nb = ctypes.c_double(), ctypes.c_double()
     _check(_L.lqs_sv_distance(ha, hb, ctypes.byref(d), ctypes.byref(nb)))
     return d.value, nb.value
+
+
+def lqs_set_jit(mode: int) -> None:
+    """Segment-compiler mode: LQS_JIT_OFF, LQS_JIT_ON or LQS_JIT_AUTO."""
+    _check(_L.lqs_set_jit(int(mode)))
+
+
+def lqs_jit_info() -> dict:
+    st = lqs_jit_stats()
+    _check(_L.lqs_jit_info(ctypes.byref(st)))
+    return {"mode": st.mode, "compiled": st.compiled, "failed": st.failed, "cached": st.cached,
+            "launches": int(st.launches), "compile_seconds": float(st.compile_seconds),
+            "last_error": st.last_error.decode(errors="replace")}
+
+
+def lqs_jit_precompile(n_qubits: int, dtype, ops, params=None, arith: int = LQS_ARITH_AUTO, cfg=None) -> int:
+    """Compiles (host only) the segment kernels lqs_apply_fused would launch; returns how many."""
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    p = _params(params)
+    c = _cfg(cfg)
+    n = ctypes.c_int()
+    _check(_L.lqs_jit_precompile(int(n_qubits), _dtype_code(dtype), int(arith), oa.ptr(), oa.n, _dptr(p),
+                                 int(np.asarray(params).size) if params is not None else 0,
+                                 ctypes.byref(c) if c is not None else None, ctypes.byref(n)))
+    return n.value

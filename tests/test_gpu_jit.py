@@ -1,0 +1,103 @@
+"""Compiled segments on the GPU: straight-line kernels against the CPU
+oracle and against the register-tile interpreter on the same inputs."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import MODES, TOL, gpu_state, max_abs, set_mode
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def jit_on():
+    import paper_2508_13615_gb300 as L
+    old = L.lqs_jit_info()["mode"]
+    L.lqs_set_jit(L.LQS_JIT_ON)
+    before = L.lqs_jit_info()
+    yield L, before
+    L.lqs_set_jit(old)
+    after = L.lqs_jit_info()
+    assert after["failed"] == before["failed"], after["last_error"]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n,seed", [(14, 21), (16, 22)])
+def test_random_circuit_compiled_vs_oracle(jit_on, dtype, arith, n, seed):
+    """The whole gate set, 200 gates, from a Gaussian state."""
+    L, before = jit_on
+    set_mode(arith)
+    c = W.random_circuit(n, 200, seed=seed)
+    psi0 = W.gaussian_state(n, seed + 100)
+    with gpu_state(n, dtype, psi0) as sv:
+        sv.apply(c, fused=True)
+        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
+    assert err <= TOL[dtype], err
+    assert L.lqs_jit_info()["launches"] > before["launches"]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_controls_inside_and_outside_the_tile(jit_on, dtype, arith):
+    """Controlled gates only: controls fall on register slots, thread bits
+    and qubits outside the tile (per-tile predicates)."""
+    L, _ = jit_on
+    set_mode(arith)
+    n = 18
+    c = W.random_circuit(n, 160, seed=77, names=["CNOT", "CZ", "CRY", "Toffoli", "ControlledPhaseShift", "H", "RX"])
+    psi0 = W.gaussian_state(n, 78)
+    with gpu_state(n, dtype, psi0) as sv:
+        sv.apply(c, fused=True)
+        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
+    assert err <= TOL[dtype], err
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_compiled_matches_interpreter(dtype, arith):
+    """Same circuit, same input: the interpreter (LQS_JIT_OFF) and the
+    compiled segments (LQS_JIT_ON) agree to rounding."""
+    import paper_2508_13615_gb300 as L
+    set_mode(arith)
+    n = 20
+    out = {}
+    old = L.lqs_jit_info()["mode"]
+    try:
+        for mode in (L.LQS_JIT_OFF, L.LQS_JIT_ON):
+            L.lqs_set_jit(mode)
+            with gpu_state(n, dtype) as sv:
+                sv.apply(W.ansatz(n, 6, 8), fused=True)
+                sv.apply(W.qft(n), fused=True)
+                out[mode] = sv.numpy()
+    finally:
+        L.lqs_set_jit(old)
+    assert max_abs(out[L.LQS_JIT_OFF], out[L.LQS_JIT_ON]) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_qft_closed_form_compiled(jit_on, dtype, arith):
+    set_mode(arith)
+    n = 21
+    N = 1 << n
+    x = W.basis_index(n, 4)
+    with gpu_state(n, dtype, basis=x) as sv:
+        sv.apply(W.qft(n), fused=True)
+        got = sv.numpy()
+    ang = 2 * np.pi * ((x * np.arange(N, dtype=np.int64)) % N) / N
+    assert max_abs(got, np.exp(1j * ang) / np.sqrt(N)) <= TOL[dtype]
+
+
+def test_angles_reuse_the_compiled_kernels(jit_on):
+    """A second circuit with the same structure and new angles compiles
+    nothing and still matches the oracle."""
+    L, _ = jit_on
+    set_mode("df")
+    n = 16
+    a, b = W.ansatz(n, 3, 31), W.ansatz(n, 3, 32)
+    with gpu_state(n, "c128") as sv:
+        sv.apply(a, fused=True)
+    compiled = L.lqs_jit_info()["compiled"]
+    with gpu_state(n, "c128") as sv:
+        sv.apply(b, fused=True)
+        err = max_abs(sv.numpy(), oracle.run_circuit(b, oracle.basis_state(n, 0)))
+    assert L.lqs_jit_info()["compiled"] == compiled
+    assert err <= TOL["c128"]
