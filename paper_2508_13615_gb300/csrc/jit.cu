@@ -68,15 +68,17 @@ std::string hex32(uint32_t x) {
 
 class SegGen {
  public:
-  SegGen(int k, int r, const char* aname, int amp_bytes) : k_(k), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes) {}
+  SegGen(int k, int b, int r, const char* aname, int amp_bytes)
+      : k_(k), b_(b), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes) {}
 
   // Returns false (with a reason) for a program this generator does not take.
   bool run(const TOp* ops, int nops, int ncoef, std::string& src, std::string& kname, std::string& why);
 
  private:
-  int k_, r_, R_;
+  int k_, b_, r_, R_;
   const char* aname_;
   int sz_;
+  int xb_ = 0;  // exchange buffer of the next layout change (they alternate)
   int slot_[4] = {0, 0, 0, 0};  // register slot m -> local position
   int thr_[16] = {0};           // thread bit m -> local position
   int vm_[16];                  // register element -> variable
@@ -111,6 +113,9 @@ class SegGen {
   std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
   bool emit_op(const TOp& t);
   void emit_layout(const TOp& t);
+  int smem_read_degree() const;
+  bool store_friendly() const;
+  void emit_store();
   bool fail(const std::string& w) {
     why_ = w;
     return false;
@@ -161,22 +166,77 @@ std::string SegGen::pred(uint32_t lc, uint64_t ec, uint32_t& regc) const {
 }
 
 void SegGen::emit_layout(const TOp& t) {
-  // write the tile in the current layout, read it back in the new one
-  o_ << "    __syncthreads();\n    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+  // Write the tile in the current layout, read it back in the new one.  The
+  // exchange buffers alternate, so one barrier suffices: the previous reader
+  // of this buffer finished before the intervening exchange's barrier (or
+  // the barriers at the top of the tile loop).
+  const char* X = xb_ ? "XB" : "XA";
+  xb_ ^= 1;
+  o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
   for (int e = 0; e < R_; ++e)
-    o_ << "      lqs::st_w(&X1[sj ^ " << hex32(host_swz(je(e), sz_)) << "], " << V(e) << ");\n";
+    o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "], " << V(e) << ");\n";
   o_ << "    }\n    __syncthreads();\n";
   set_layout(t.ecmask);  // validated by the caller
   o_ << "    jt = " << jt_expr() << ";\n    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
   for (int e = 0; e < R_; ++e) {
     vm_[e] = e;
-    o_ << "      v" << e << " = lqs::ld_w(&X1[sj ^ " << hex32(host_swz(je(e), sz_)) << "]);\n";
+    o_ << "      v" << e << " = lqs::ld_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "]);\n";
   }
   o_ << "    }\n";
   if (t.e0 != t.ecmask) {  // relabelling SWAPs: from here on amplitudes carry their logical positions
     set_layout(t.e0);
     o_ << "    jt = " << jt_expr() << ";\n";
   }
+}
+
+// Worst shared-memory bank conflict of reading the unswizzled incoming tile
+// in the current layout: a warp access is served in phases of 128 bytes, and
+// lanes of one phase whose amplitudes share a 4-bank group conflict.
+int SegGen::smem_read_degree() const {
+  const int per_phase = 128 / sz_;
+  int worst = 1;
+  for (int ph = 0; ph < 32 / per_phase; ++ph) {
+    int cnt[32] = {0};
+    for (int l = ph * per_phase; l < (ph + 1) * per_phase; ++l) {
+      uint32_t j = 0;
+      for (int m = 0; m < 5 && m < k_ - r_; ++m)
+        if ((l >> m) & 1) j |= 1u << thr_[m];
+      worst = std::max(worst, ++cnt[j % per_phase]);
+    }
+  }
+  return worst;
+}
+
+// Global stores straight from registers write whole 32-byte sectors when the
+// amplitudes of each sector (the lowest tile positions) sit on lane bits.
+bool SegGen::store_friendly() const {
+  const int need = 32 / sz_;  // amplitudes per sector: positions 0 .. log2(need)-1
+  uint32_t lanes = 0;
+  for (int m = 0; m < 5 && m < k_ - r_; ++m) lanes |= 1u << thr_[m];
+  const uint32_t want = (uint32_t)need - 1u;
+  return (lanes & want) == want && b_ >= (need == 4 ? 2 : 1);
+}
+
+// The result leaves registers for HBM directly: local index j of the tile is
+// amplitude base + (j mod 2^b) + (row j >> b placed on the high tile qubits).
+// The thread part of the offset is formed once per thread; the register part
+// is a sum of per-slot terms.
+void SegGen::emit_store() {
+  pre_ << "  uint64_t st_t;\n  { const uint32_t j = " << jt_expr() << ";\n"
+       << "    st_t = (uint64_t)(j & " << hex32((1u << b_) - 1u) << ") + lqs::row_offset(G, j >> " << b_ << "); }\n";
+  for (int m = 0; m < r_; ++m) {
+    const int p = slot_[m];
+    if (p < b_) pre_ << "  const uint64_t st_" << m << " = " << (1u << p) << "ull;\n";
+    else pre_ << "  const uint64_t st_" << m << " = 1ull << G.h[" << (p - b_) << "];\n";
+  }
+  o_ << "    { S* out = psi + base + st_t;\n";
+  for (int e = 0; e < R_; ++e) {
+    std::string off;
+    for (int m = 0; m < r_; ++m)
+      if ((e >> m) & 1) off += (off.empty() ? "" : " + ") + ("st_" + std::to_string(m));
+    o_ << "      out[" << (off.empty() ? std::string("0") : off) << "] = A::store(" << V(e) << ");\n";
+  }
+  o_ << "    }\n";
 }
 
 bool SegGen::emit_op(const TOp& t) {
@@ -413,10 +473,10 @@ extern "C" __global__ void __launch_bounds__(256, 2)
   typedef A::C C;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const lqs::TileGeom& G = P.g;
-  S* S0 = reinterpret_cast<S*>(smem_raw);
-  S* S1 = S0 + @NT@;
-  W* X1 = reinterpret_cast<W*>(S1);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(S1 + @NT@);
+  S* S0 = reinterpret_cast<S*>(smem_raw);  // incoming tiles (bulk loads, prefetched one tile ahead)
+  W* XA = reinterpret_cast<W*>(S0 + @NT@);  // layout exchanges alternate between XA and XB
+  W* XB = XA + @NT@;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(XB + @NT@);
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
     lqs::mbar_init(bar, 1);
@@ -434,11 +494,7 @@ extern "C" __global__ void __launch_bounds__(256, 2)
     if (!ok) break;
 )";
 
-const char* kSkeletonTail = R"(    lqs::fence_proxy_async();
-    __syncthreads();
-    if (tid < 32) lqs::tile_store_issue(G, psi, S1, base);
-  }
-  if (tid < 32) lqs::bulk_wait0();
+const char* kSkeletonTail = R"(  }
   if (!ok && tid == 0) {
     lqs::flag_timeout(status, 4);
     lqs::mbar_wait(bar, phase ^ 1u);
@@ -472,23 +528,53 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::str
         return false;
       }
     }
-  // the first layout loads the incoming tile
-  set_layout(ops[0].ecmask);
+  // The incoming tile is in natural order.  The program's first layout reads
+  // it as is; when the next op is already a layout change whose reads of the
+  // unswizzled tile conflict at most 2-way, the tile is read in that layout
+  // directly and the exchange is skipped.
+  int first = 1;
+  uint64_t through = ops[0].ecmask, logical = ops[0].e0;
+  if (nops > 1 && ops[1].kind == K_LAYOUT) {
+    set_layout(ops[1].ecmask);
+    if (smem_read_degree() <= 2) {
+      through = ops[1].ecmask;
+      logical = ops[1].e0;
+      first = 2;
+    }
+  }
+  set_layout(through);
   for (int e = 0; e < R_; ++e) vm_[e] = e;
   o_ << "    uint32_t jt = " << jt_expr() << ";\n";
   o_ << "    W";
   for (int e = 0; e < R_; ++e) o_ << (e ? ", v" : " v") << e;
   o_ << ";\n";
   for (int e = 0; e < R_; ++e) o_ << "    v" << e << " = A::load(S0[jt + " << hex32(je(e)) << "]);\n";
-  if (ops[0].e0 != ops[0].ecmask) {
-    set_layout(ops[0].e0);
+  if (logical != through) {
+    set_layout(logical);
     o_ << "    jt = " << jt_expr() << ";\n";
   }
   o_ << "    __syncthreads();  // the incoming buffer is free: prefetch the next tile into it\n"
         "    { const uint64_t tn = t + gridDim.x;\n"
         "      if (tn < G.ntiles && tid < 32) lqs::tile_load_issue(G, S0, psi, lqs::tile_base(G, tn), bar); }\n";
-  for (int i = 1; i < nops; ++i) {
+  for (int i = first; i < nops; ++i) {
     if (ops[i].kind == K_LAYOUT) {
+      if (i == nops - 1) {
+        // The closing layout only restores natural order for the store.  Direct
+        // stores need no particular order, so when the current layout, mapped
+        // from storage positions to the positions they stand for (relabelled
+        // SWAPs), keeps sectors on lane bits, the exchange is skipped.
+        int L[16];
+        for (int q = 0; q < k_; ++q)
+          L[(ops[i].ecmask >> (4 * q)) & 15u] = (int)((ops[i].e0 >> (4 * q)) & 15u);
+        const int saved_slot[4] = {slot_[0], slot_[1], slot_[2], slot_[3]};
+        int saved_thr[16];
+        std::copy(thr_, thr_ + 16, saved_thr);
+        for (int m = 0; m < r_; ++m) slot_[m] = L[slot_[m]];
+        for (int m = 0; m < k_ - r_; ++m) thr_[m] = L[thr_[m]];
+        if (store_friendly()) break;
+        std::copy(saved_slot, saved_slot + 4, slot_);
+        std::copy(saved_thr, saved_thr + 16, thr_);
+      }
       emit_layout(ops[i]);
       continue;
     }
@@ -497,10 +583,10 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::str
       return false;
     }
   }
-  o_ << "    __syncthreads();  // exchange readers are done before the result overwrites the buffer\n";
-  for (int e = 0; e < R_; ++e) o_ << "    S1[jt + " << hex32(je(e)) << "] = A::store(" << V(e) << ");\n";
+  emit_store();  // natural order, or a layout that keeps sectors on lanes
   const std::string body = o_.str();
-  const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^ fnv1a(aname_);
+  const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^
+                     ((uint64_t)b_ << 36) ^ fnv1a(aname_);
   char nm[40];
   std::snprintf(nm, sizeof nm, "lqs_seg_%016llx", (unsigned long long)h);
   kname = nm;
@@ -759,7 +845,7 @@ template <> struct JitTypeName<ArDF> { static constexpr const char* s = "lqs::Ar
 
 template <class A>
 int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why) {
-  SegGen g(P.g.k, r, JitTypeName<A>::s, A::kAmpBytes);
+  SegGen g(P.g.k, P.g.b, r, JitTypeName<A>::s, A::kAmpBytes);
   return g.run(P.op, P.nops, P.ncoef, src, name, why) ? LQS_OK : LQS_ERR_UNSUPPORTED;
 }
 
@@ -823,7 +909,7 @@ int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, 
   if (!e || e->state != 1) return LQS_OK;
   const int dev = sv->device;
   if (dev < 0 || dev >= kJitMaxDevices) return LQS_OK;
-  const size_t smem = 2 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;
+  const size_t smem = 3 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;  // incoming tile, two exchange buffers
   CUfunction fn;
   int per_sm;
   {
