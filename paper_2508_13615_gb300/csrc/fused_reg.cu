@@ -464,7 +464,7 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
 
   // 2. layouts and emission
   auto nondiag = [&](const Ent& e) { return e.op >= 0 && !ops[e.op].diagonal(); };
-  auto choose = [&](size_t i) {
+  auto choose = [&](size_t i, const std::vector<int>& keep) {
     std::vector<int> slot(r, -1);
     auto has = [&](int q) { return std::find(slot.begin(), slot.end(), q) != slot.end(); };
     auto put = [&](int q) {
@@ -489,8 +489,11 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       put(lp(o.t0));
       if (std::count(slot.begin(), slot.end(), -1) == 0) break;
     }
-    // fill with the highest unused local qubits, leaving low qubits to the
-    // thread (lane) bits so shared-memory rows stay contiguous
+    // fill with qubits already in registers (nothing moves for them), then
+    // with the highest unused local qubits, leaving low qubits to the thread
+    // (lane) bits so shared-memory rows stay contiguous
+    for (int q : keep)
+      if (std::count(slot.begin(), slot.end(), -1)) put(q);
     for (int q = k - 1; q >= 0 && std::count(slot.begin(), slot.end(), -1); --q) put(q);
     return slot;
   };
@@ -513,12 +516,47 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       if (pi[l] != l) return false;
     return true;
   };
-  auto emit_layout = [&](const std::vector<int>& slot) -> int {
+  // Thread bits that keep their storage position across a layout change do
+  // not move data between the threads they select, so an exchange confined
+  // to those groups of threads (often a single warp) needs no block-wide
+  // barrier.  A new layout therefore keeps every thread bit whose position
+  // stays out of the registers where it was; only the bits vacated by the
+  // new register qubits take the qubits that leave the registers.
+  uint64_t prev_logical = 0;
+  bool have_prev = false;
+  auto pack_keep = [&](const std::vector<int>& slot) {
+    std::vector<int> pinv(k);
+    for (int l = 0; l < k; ++l) pinv[pi[l]] = l;
+    std::vector<char> used(k, 0);
+    for (int m = 0; m < r; ++m) used[slot[m]] = 1;
+    std::vector<int> thr(k - r, -1);
+    for (int m = 0; m < k - r; ++m) {
+      const int l = pinv[(prev_logical >> (4 * (r + m))) & 15];  // where the bit's data sits now, as a qubit
+      if (!used[l]) {
+        thr[m] = l;
+        used[l] = 1;
+      }
+    }
+    int q = 0;
+    for (int m = 0; m < k - r; ++m) {
+      if (thr[m] >= 0) continue;
+      while (used[q]) ++q;
+      thr[m] = q;
+      used[q] = 1;
+    }
+    uint64_t p = 0;
+    for (int m = 0; m < r; ++m) p |= (uint64_t)slot[m] << (4 * m);
+    for (int m = 0; m < k - r; ++m) p |= (uint64_t)thr[m] << (4 * (r + m));
+    return p;
+  };
+  auto emit_layout = [&](const std::vector<int>& slot, bool keep) -> int {
     if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;  // the caller splits the segment
     TOp t{};
     t.kind = K_LAYOUT;
     t.gslot = -1;
-    const uint64_t logical = pack(slot);
+    const uint64_t logical = keep && have_prev ? pack_keep(slot) : pack(slot);
+    prev_logical = logical;
+    have_prev = true;
     uint64_t through = 0;  // the same layout with each position mapped through pi
     for (int i = 0; i < k; ++i) through |= (uint64_t)pi[(logical >> (4 * i)) & 15] << (4 * i);
     t.ecmask = through;
@@ -534,7 +572,7 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
   std::vector<int> natural(r);
   for (int m = 0; m < r; ++m) natural[m] = k - r + m;
   std::vector<int> cur = natural;
-  LQS_TRY(emit_layout(cur));
+  LQS_TRY(emit_layout(cur, false));
   for (size_t i = 0; i < seq.size(); ++i) {
     if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
     if (seq[i].op >= 0) {
@@ -592,8 +630,12 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       const bool fits = two_target(o) ? (cur[1] == a && cur[0] == b)
                                       : std::find(cur.begin(), cur.end(), a) != cur.end();
       if (!fits) {
-        cur = choose(i);
-        LQS_TRY(emit_layout(cur));  // resets the relabelling
+        std::vector<int> keep(r);  // the qubits now held in registers
+        for (int m = 0; m < r; ++m)
+          for (int l = 0; l < k; ++l)
+            if (pi[l] == cur[m]) keep[m] = l;
+        cur = choose(i, keep);
+        LQS_TRY(emit_layout(cur, true));  // resets the relabelling
         if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
       }
     }
@@ -618,7 +660,7 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       t.s1 = o.t1 >= 0 ? (int8_t)(std::find(cur.begin(), cur.end(), pp(o.t1)) - cur.begin()) : (int8_t)-1;
     }
   }
-  if (cur != natural || !is_identity()) LQS_TRY(emit_layout(natural));
+  if (cur != natural || !is_identity()) LQS_TRY(emit_layout(natural, false));
   return LQS_OK;
 }
 

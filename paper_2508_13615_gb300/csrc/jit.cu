@@ -78,7 +78,8 @@ class SegGen {
   int k_, b_, r_, R_;
   const char* aname_;
   int sz_;
-  int xb_ = 0;  // exchange buffer of the next layout change (they alternate)
+  int xb_ = 0;        // exchange buffer of the next layout change (they alternate)
+  int next_bar_ = 1;  // next free named barrier id in this tile iteration (0 is the block barrier)
   int slot_[4] = {0, 0, 0, 0};  // register slot m -> local position
   int thr_[16] = {0};           // thread bit m -> local position
   int vm_[16];                  // register element -> variable
@@ -172,10 +173,44 @@ void SegGen::emit_layout(const TOp& t) {
   // the barriers at the top of the tile loop).
   const char* X = xb_ ? "XB" : "XA";
   xb_ ^= 1;
+  // Warp-index thread bits that keep their position confine the exchange to
+  // the warps agreeing on them (each group keeps its set of amplitudes), so
+  // only those warps synchronise: __syncwarp when no warp bit moves, a named
+  // barrier per group when some do, the block barrier when all do.
+  uint32_t fixed = 0, moved = 0;
+  for (int m = 5; m < k_ - r_; ++m) {
+    const int to = (int)((t.ecmask >> (4 * (r_ + m))) & 15u);
+    if (to == thr_[m]) fixed |= 1u << m;
+    else moved |= 1u << m;
+  }
+  // Every group barrier of a tile iteration gets ids of its own: a warp may
+  // reach a later exchange while warps of another group are still at an
+  // earlier one, and two barrier instances must never share an id.  When the
+  // ids run out the block barrier is used; the block barriers at the top of
+  // the tile loop make all ids free again.
+  const int groups = 1 << __builtin_popcount(fixed);
+  std::string bar;
+  if (!moved) {
+    bar = "__syncwarp();";
+  } else if (!fixed || next_bar_ + groups - 1 > 15) {
+    bar = "__syncthreads();";
+    next_bar_ = 1;  // every warp passes it after all earlier group barriers completed
+  } else {
+    std::string id;
+    int j = 0;
+    for (int m = 5; m < k_ - r_; ++m)
+      if ((fixed >> m) & 1u) {
+        id += " + (((tid >> " + std::to_string(m) + ") & 1u) << " + std::to_string(j) + ")";
+        ++j;
+      }
+    bar = "lqs::jit::bar_group(" + std::to_string(next_bar_) + "u" + id + ", " +
+          std::to_string(32u << __builtin_popcount(moved)) + "u);";
+    next_bar_ += groups;
+  }
   o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
   for (int e = 0; e < R_; ++e)
     o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "], " << V(e) << ");\n";
-  o_ << "    }\n    __syncthreads();\n";
+  o_ << "    }\n    " << bar << "\n";
   set_layout(t.ecmask);  // validated by the caller
   o_ << "    jt = " << jt_expr() << ";\n    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
   for (int e = 0; e < R_; ++e) {
@@ -478,13 +513,15 @@ extern "C" __global__ void __launch_bounds__(256, 2)
   W* XB = XA + @NT@;
   uint64_t* bar = reinterpret_cast<uint64_t*>(XB + @NT@);
   const uint32_t tid = threadIdx.x;
+  uint64_t t = blockIdx.x;
   if (tid == 0) {
     lqs::mbar_init(bar, 1);
     lqs::fence_mbar_init();
+    if (t < G.ntiles) lqs::jit::seg_expect(G, bar);
   }
   __syncthreads();
-  uint64_t t = blockIdx.x;
-  if (t < G.ntiles && tid < 32) lqs::tile_load_issue(G, S0, psi, lqs::tile_base(G, t), bar);
+  const uint64_t my_roff = tid < (1u << G.r) ? lqs::row_offset(G, tid) : 0ull;
+  if (t < G.ntiles) lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, t), bar, my_roff);
   uint32_t phase = 0;
   bool ok = true;
 @PRE@  for (; t < G.ntiles; t += gridDim.x) {
@@ -492,6 +529,8 @@ extern "C" __global__ void __launch_bounds__(256, 2)
     ok = __syncthreads_and(lqs::mbar_wait(bar, phase));
     phase ^= 1u;
     if (!ok) break;
+    // the next phase's byte count goes up before any of its copies is issued
+    if (tid == 0 && t + gridDim.x < G.ntiles) lqs::jit::seg_expect(G, bar);
 )";
 
 const char* kSkeletonTail = R"(  }
@@ -555,7 +594,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::str
   }
   o_ << "    __syncthreads();  // the incoming buffer is free: prefetch the next tile into it\n"
         "    { const uint64_t tn = t + gridDim.x;\n"
-        "      if (tn < G.ntiles && tid < 32) lqs::tile_load_issue(G, S0, psi, lqs::tile_base(G, tn), bar); }\n";
+        "      if (tn < G.ntiles) lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, tn), bar, my_roff); }\n";
   for (int i = first; i < nops; ++i) {
     if (ops[i].kind == K_LAYOUT) {
       if (i == nops - 1) {

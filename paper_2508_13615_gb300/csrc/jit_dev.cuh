@@ -9,6 +9,7 @@
 // products and sums.
 #pragma once
 #include "arith.cuh"
+#include "tile.cuh"
 
 namespace lqs {
 namespace jit {
@@ -73,6 +74,31 @@ template <int SZ>
 __device__ __forceinline__ uint32_t swz(uint32_t j) {
   if (SZ == 16) return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7u);
   return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
+}
+
+// Issues the bulk copies of one tile into `buf`, one row per thread (rows
+// beyond the block size wrap): the work is spread over the block instead of
+// one warp, so no warp falls behind the others before the next barrier.
+// `my_roff` is row_offset(G, tid), formed once per launch.  The phase's
+// expected byte count (its only arrival) must already be posted by thread 0
+// (seg_expect) before any thread issues a copy of that phase.
+template <class S>
+__device__ __forceinline__ void seg_copy(const TileGeom& G, S* buf, const S* psi, uint64_t base, uint64_t* bar,
+                                         uint64_t my_roff) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nrows = 1u << G.r;
+  const uint32_t per_row = 1u << G.b;
+  for (uint32_t row = tid; row < nrows; row += blockDim.x)
+    bulk_g2s(buf + (size_t)row * per_row, psi + base + (row == tid ? my_roff : row_offset(G, row)), G.row_bytes, bar);
+}
+__device__ __forceinline__ void seg_expect(const TileGeom& G, uint64_t* bar) {
+  mbar_expect_tx(bar, (1u << G.r) * G.row_bytes);
+}
+
+// Barrier over a group of warps: named barrier `id` (1..15; 0 is the
+// block-wide barrier) for `nthreads` threads, a multiple of 32.
+__device__ __forceinline__ void bar_group(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 }  // namespace jit

@@ -60,3 +60,33 @@ def test_small_states_have_no_segments_to_compile():
     """States that fit one tile never use the register-tile kernel."""
     c = W.ansatz(8, 3, 2)
     assert L.lqs_jit_precompile(8, "c128", c.ops, c.params, L.LQS_ARITH_DF) == 0
+
+
+def test_named_barriers_are_never_shared(tmp_path, monkeypatch):
+    """Generated kernels give every group barrier of a tile iteration ids of
+    its own (a warp may reach a later exchange while another group is still
+    at an earlier one); ids are reused only after a block-wide barrier."""
+    import glob
+    import re
+    monkeypatch.setenv("LQS_JIT_DUMP", str(tmp_path))
+    for dtype, arith, n in (("c128", L.LQS_ARITH_DF, 19), ("c64", L.LQS_ARITH_AUTO, 19)):
+        for seed in (61, 62):
+            c = W.random_circuit(n, 160, seed=seed)
+            L.lqs_jit_precompile(n, dtype, c.ops, c.params, arith)
+    files = glob.glob(str(tmp_path / "*.cu"))
+    assert files
+    groups = 0
+    for f in files:
+        body = open(f).read().split("for (; t < G.ntiles; t += gridDim.x) {", 1)[1]
+        used = set()
+        for line in body.splitlines():
+            if "__syncthreads" in line:
+                used = set()
+            m = re.search(r"bar_group\((\d+)u(.*), (\d+)u\);", line)
+            if m:
+                groups += 1
+                ids = set(range(int(m.group(1)), int(m.group(1)) + (1 << m.group(2).count("tid >>"))))
+                assert not ids & used and max(ids) <= 15, (f, line)
+                assert int(m.group(3)) * len(ids) == 256, line  # the groups cover the block exactly
+                used |= ids
+    assert groups > 0
