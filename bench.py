@@ -292,8 +292,15 @@ def config_adjoint24(args):
     terms = W.tfim(n)
     ops = L.OpArray(c.ops)
     pa = L.PauliArray(terms)
-    out = {"config": "adjoint24", "metric": "adjoint/forward time", "n_qubits": n, "params": c.n_params}
+    out = {"config": "adjoint24", "metric": "adjoint/forward time", "n_qubits": n, "params": c.n_params,
+           "kernels": "compiled fused segments forward, compiled reverse sweep (psi and lambda in registers)"}
+    L.lqs_set_jit(L.LQS_JIT_ON)
     for dtype in ("c128", "c64"):
+        ar = L.LQS_ARITH_DF if dtype == "c128" else L.LQS_ARITH_AUTO
+        t_jit = time.perf_counter()
+        L.lqs_jit_precompile(n, dtype, c.ops, c.params, ar)
+        L.lqs_jit_precompile_adjoint(n, dtype, c.ops, c.params, ar)
+        jit_s = time.perf_counter() - t_jit
         sv = L.StateVector(n, dtype)
         st = torch.cuda.current_stream()
 
@@ -319,7 +326,8 @@ def config_adjoint24(args):
             torch.cuda.synchronize()
             ta.append(e0.elapsed_time(e1))
         rec = {"forward_ms": statistics.median(tf), "adjoint_ms": statistics.median(ta),
-               "adjoint_over_forward": statistics.median(ta) / statistics.median(tf), "energy": e}
+               "adjoint_over_forward": statistics.median(ta) / statistics.median(tf), "energy": e,
+               "compile_wall_s": round(jit_s, 2)}
         if dtype == "c128":
             h = 1e-6
             fd = []

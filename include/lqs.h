@@ -309,6 +309,14 @@ LQS_API int lqs_jit_info(lqs_jit_stats* out);
  * NVRTC cannot be loaded or rejects a segment (lqs_last_error has its log). */
 LQS_API int lqs_jit_precompile(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops,
                                const double* params, int n_params, const lqs_fuse_cfg* cfg, int* n_compiled);
+/* The same for the reverse sweep of lqs_adjoint_grad on this circuit: its compiled kernels hold psi and
+ * lambda in registers (tiles one qubit smaller than lqs_apply_fused's, 128 threads) and add each
+ * parameter's Im<lambda|G|psi> as they un-apply the gates.  lqs_adjoint_grad uses them whenever compiled
+ * segments are enabled for the state's size (LQS_JIT_ON, or LQS_JIT_AUTO on 20 or more qubits),
+ * compiling missing ones at that call; states of at most 10 (c128) / 11 (c64) qubits use the
+ * shared-memory sweep and compile nothing here. */
+LQS_API int lqs_jit_precompile_adjoint(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops,
+                                       const double* params, int n_params, int* n_compiled);
 
 /* Per-launch profile records (tracing).  Between lqs_profile_start and
  * lqs_profile_stop every kernel the library launches is bracketed by CUDA

@@ -8,6 +8,7 @@
 
 #include "arith.cuh"
 #include "jit.h"
+#include "measure_common.cuh"
 #include "lqs_internal.cuh"
 
 namespace lqs {
@@ -425,6 +426,23 @@ int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* param
   }
   for (const Segment& s : segs) LQS_TRY(launch_segment(sv, kops, s, pc, arith));
   return LQS_OK;
+}
+
+int lqs_jit_precompile_adjoint(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops,
+                               const double* params, int n_params, int* n_compiled) {
+  if (n_compiled) *n_compiled = 0;
+  if (n_qubits < 1 || n_qubits > 36) return set_error(LQS_ERR_ARG, "n_qubits must be in [1, 36]");
+  if (dtype != LQS_C64 && dtype != LQS_C128) return set_error(LQS_ERR_ARG, "bad dtype");
+  if (arith != LQS_ARITH_AUTO && arith != LQS_ARITH_F64 && arith != LQS_ARITH_DF)
+    return set_error(LQS_ERR_ARG, "arith must be LQS_ARITH_AUTO, LQS_ARITH_F64 or LQS_ARITH_DF");
+  std::vector<KOp> kops;
+  LQS_TRY(lower_ops(n_qubits, ops, n_ops, params, n_params, true, kops));
+  std::vector<KOp> rev;
+  rev.reserve(kops.size());
+  for (size_t i = kops.size(); i-- > 0;) rev.push_back(inverse_op(kops[i]));
+  const int ar = current_arith(arith);
+  if (n_qubits <= adjoint_tile_qubits(dtype)) return LQS_OK;  // one tile: the interpreter sweep runs it
+  return adjoint_precompile(n_qubits, dtype, ar, rev, n_compiled);
 }
 
 int lqs_jit_precompile(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops, const double* params,

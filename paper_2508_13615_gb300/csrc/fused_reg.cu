@@ -17,6 +17,9 @@
 // and stored by bulk copies.
 #include <algorithm>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <memory>
 #include <string>
 #include <type_traits>
 
@@ -32,6 +35,7 @@ template <class A> int add_tile_op(TileProg<A>& P, const KOp& o, int gslot);
 template <class A> void init_prog(TileProg<A>& P, int n, uint64_t Q, int k, int b);
 
 constexpr int kRegThreadBits = 8;
+constexpr int kMaxGradSlotsReg = 128;  // gradient slots per compiled adjoint segment
 constexpr int kRegThreads = 1 << kRegThreadBits;
 
 template <int R> struct RLog;
@@ -410,7 +414,14 @@ struct Ent {
 };
 
 template <class A>
-static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Segment& seg, int r) {
+static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Segment& seg, int r,
+                          std::vector<int>* grad_ops = nullptr) {
+  // grad_ops (compiled adjoint): every parametrised op gets a gradient slot
+  // in emission order and grad_ops receives the op of each slot; members of
+  // merged diagonal runs are emitted as K_GRAD partials just before their run
+  // (diagonal unitaries leave conj(lambda_j) psi_j unchanged, and the run only
+  // moved past ops on other wires, which commute with its generators).
+  auto has_grad = [&](const KOp& o) { return grad_ops && o.param_slot >= 0 && o.gen != G_NONE; };
   const TileGeom& G = P.g;
   const int k = G.k;
   auto lp = [&](int q) -> int {
@@ -590,6 +601,30 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
     };
     if (seq[i].group >= 0) {
       const DGroup& g = groups[seq[i].group];
+      for (int mi : g.members) {
+        const KOp& mo = ops[mi];
+        if (!has_grad(mo)) continue;
+        if (P.nops >= kMaxTileOps || (int)grad_ops->size() >= kMaxGradSlotsReg) return LQS_ERR_UNSUPPORTED;
+        TOp t{};
+        t.kind = K_GRAD;
+        t.gen = (uint8_t)mo.gen;
+        t.gslot = (int16_t)grad_ops->size();
+        t.l0 = t.l1 = -1;
+        t.s0 = t.s1 = -1;
+        if (mo.t0 >= 0) {
+          const int l = pp(mo.t0);
+          if (l >= 0) t.l0 = (int8_t)l;
+          else t.e0 = 1ull << mo.t0;
+        }
+        for (int q = 0; q < G.n; ++q) {
+          if (!((mo.cmask >> q) & 1)) continue;
+          const int l = pp(q);
+          if (l >= 0) t.lcmask |= 1u << l;
+          else t.ecmask |= 1ull << q;
+        }
+        P.op[P.nops++] = t;
+        grad_ops->push_back(mi);
+      }
       auto f = g.f;
       // local factors in increasing storage position, then outside factors by qubit
       std::sort(f.begin(), f.end(), [&](const auto& x, const auto& y) {
@@ -639,7 +674,13 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
         if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
       }
     }
-    const int rc = add_tile_op(P, o, -1);
+    int gslot = -1;
+    if (has_grad(o)) {
+      if ((int)grad_ops->size() >= kMaxGradSlotsReg) return LQS_ERR_UNSUPPORTED;
+      gslot = (int)grad_ops->size();
+      grad_ops->push_back(seq[i].op);
+    }
+    const int rc = add_tile_op(P, o, gslot);
     if (rc != LQS_OK) return LQS_ERR_UNSUPPORTED;
     TOp& t = P.op[P.nops - 1];
     if (!is_identity()) {  // translate the op's local positions to storage positions
@@ -713,6 +754,153 @@ int note_reg_prog(int n, int dtype, int arith, const std::vector<KOp>& ops, cons
   if (dtype == LQS_C64) return note_reg_prog_t<ArF32>(n, ops, seg, k, b, force, todo);
   if (arith == LQS_ARITH_F64) return note_reg_prog_t<ArF64>(n, ops, seg, k, b, force, todo);
   return note_reg_prog_t<ArDF>(n, ops, seg, k, b, force, todo);
+}
+
+// ---------------------------------------------------------------------------
+// compiled adjoint (reverse sweep over psi and lambda)
+// ---------------------------------------------------------------------------
+// Tiles one qubit smaller than the forward kernel's, with 128 threads: the
+// kernel holds two states in registers and four tiles in shared memory
+// (incoming psi and lambda, two exchange buffers), three CTAs per SM.
+// Shape of the compiled adjoint: register bits per state and thread bits.
+// Measured on GB300 (24-qubit ansatz): complex128 runs fastest with 4
+// amplitudes of each state per thread and 256 threads (half the code per
+// op, 16 warps per SM), complex64 with 16 per state and 128 threads.
+static void adj_shape(int dtype, int* r, int* tb) {
+  *r = dtype == LQS_C64 ? 4 : 2;
+  *tb = dtype == LQS_C64 ? 7 : 8;
+}
+int adjoint_tile_qubits(int dtype) {
+  int r, tb;
+  adj_shape(dtype, &r, &tb);
+  return r + tb;
+}
+
+bool reg_adjoint_available(const SV* sv, int) {
+  return jit_enabled_for(sv->n) && sv->n > adjoint_tile_qubits(sv->dtype);
+}
+
+template <class A>
+struct AdjProg {
+  TileProg<A> P;
+  std::vector<int> gops;  // op (index into rev) of each gradient slot
+  std::vector<int> ops;   // the segment's ops (for the profile's flop count)
+  void* entry = nullptr;
+};
+
+template <class A>
+static int adj_build(int n, const std::vector<KOp>& rev, const Segment& seg, int k, int b, int r,
+                     std::vector<std::unique_ptr<AdjProg<A>>>& out) {
+  auto pr = std::make_unique<AdjProg<A>>();
+  init_prog(pr->P, n, seg.qmask, k, b);
+  const int rc = build_reg_prog(pr->P, rev, seg, r, &pr->gops);
+  if (rc == LQS_OK) {
+    pr->P.ngrad = (int)pr->gops.size();
+    pr->ops = seg.ops;
+    out.push_back(std::move(pr));
+    return LQS_OK;
+  }
+  if (rc != LQS_ERR_UNSUPPORTED || seg.ops.size() < 2) return rc;
+  Segment lo, hi;  // too many ops, coefficients or gradient slots: split in order
+  lo.qmask = hi.qmask = seg.qmask;
+  lo.ops.assign(seg.ops.begin(), seg.ops.begin() + seg.ops.size() / 2);
+  hi.ops.assign(seg.ops.begin() + seg.ops.size() / 2, seg.ops.end());
+  LQS_TRY(adj_build(n, rev, lo, k, b, r, out));
+  return adj_build(n, rev, hi, k, b, r, out);
+}
+
+// Plans the reverse sweep, builds its programs and compiles the missing
+// kernels (host only).  *compiled (optional) gets the number of kernels this
+// call compiled.
+template <class A>
+static int adj_prepare_t(int n, int dtype, const std::vector<KOp>& rev, std::vector<std::unique_ptr<AdjProg<A>>>& progs,
+                         int* compiled) {
+  int r, tb;
+  adj_shape(dtype, &r, &tb);
+  const int k = r + tb, b = dtype == LQS_C64 ? 5 : 4;
+  if (n <= k) return set_error(LQS_ERR_UNSUPPORTED, "state fits one adjoint tile");
+  PlanCfg pc;
+  pc.k = k;
+  pc.b = b;
+  pc.max_ops = kMaxTileOps;
+  std::vector<Segment> segs;
+  LQS_TRY(plan_segments(n, rev, pc, segs));
+  for (const Segment& sg : segs) LQS_TRY(adj_build(n, rev, sg, k, b, r, progs));
+  std::vector<void*> todo;
+  for (auto& pr : progs) {
+    std::string why;
+    if (jit_adjoint_entry(pr->P, r, &pr->entry, &why) != LQS_OK)
+      return set_error(LQS_ERR_UNSUPPORTED, "adjoint segment not compiled: " + why);
+    if (std::find(todo.begin(), todo.end(), pr->entry) == todo.end()) todo.push_back(pr->entry);
+  }
+  int before = 0;
+  std::string err;
+  jit_states(todo, &before, &err);
+  LQS_TRY(jit_compile(todo));
+  int good = 0;
+  if (jit_states(todo, &good, &err) != LQS_OK) return set_error(LQS_ERR_UNSUPPORTED, "adjoint segment: " + err);
+  if (compiled) *compiled = good - before;
+  return LQS_OK;
+}
+
+template <class A>
+static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam, int arith,
+                                  std::vector<int>& slot_op, double** partial_out, int* grid_out) {
+  int r, tb;
+  adj_shape(sv->dtype, &r, &tb);
+  const int n = sv->n, k = r + tb;
+  std::vector<std::unique_ptr<AdjProg<A>>> progs;
+  LQS_TRY(adj_prepare_t<A>(n, sv->dtype, rev, progs, nullptr));
+  size_t nslots = 0;
+  for (auto& pr : progs) nslots += pr->gops.size();
+  // one grid for all segments (the partial sums share a layout): as many
+  // CTAs as the least occupant kernel keeps resident
+  int per_sm = 8;
+  for (auto& pr : progs) {
+    int ps = 0;
+    LQS_TRY(jit_adjoint_occupancy(pr->entry, pr->P, r, sv, &ps));
+    per_sm = std::min(per_sm, ps);
+  }
+  const uint64_t ntiles = 1ull << (n - k);
+  const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)std::max(sv->sms, 1) * std::max(per_sm, 1));
+  void* scratch = nullptr;
+  LQS_TRY(sv_scratch(sv, 1, sizeof(double) * (std::max<size_t>(nslots, 1) * (grid + 1)), &scratch));
+  double* partial = static_cast<double*>(scratch);
+  const std::string pname = std::string("k_adjoint_jit/") + arith_tag(sv->dtype, arith);
+  size_t off = 0;
+  for (auto& pr : progs) {
+    // both states un-apply every op; each gradient slot is about 8 flops per amplitude
+    double fl = 8.0 * (double)pr->gops.size();
+    for (int i : pr->ops) fl += 2.0 * kop_touched_fraction(rev[i]) * kop_flops_per_amp(rev[i]);
+    LQS_TRY(jit_launch_adjoint(pr->entry, pr->P, r, sv, lam, partial + off * grid, grid, 4.0 * (double)sv->bytes(),
+                               fl * (double)sv->N(), pname.c_str()));
+    off += pr->gops.size();
+    slot_op.insert(slot_op.end(), pr->gops.begin(), pr->gops.end());
+  }
+  *partial_out = partial;
+  *grid_out = (int)grid;
+  return LQS_OK;
+}
+
+int adjoint_precompile(int n, int dtype, int arith, const std::vector<KOp>& rev, int* compiled) {
+  if (dtype == LQS_C64) {
+    std::vector<std::unique_ptr<AdjProg<ArF32>>> p;
+    return adj_prepare_t<ArF32>(n, dtype, rev, p, compiled);
+  }
+  if (arith == LQS_ARITH_F64) {
+    std::vector<std::unique_ptr<AdjProg<ArF64>>> p;
+    return adj_prepare_t<ArF64>(n, dtype, rev, p, compiled);
+  }
+  std::vector<std::unique_ptr<AdjProg<ArDF>>> p;
+  return adj_prepare_t<ArDF>(n, dtype, rev, p, compiled);
+}
+
+int run_adjoint_compiled(SV* sv, const std::vector<KOp>& rev, void* lam, int arith, std::vector<int>& slot_op,
+                         double** partial, int* grid) {
+  slot_op.clear();
+  if (sv->dtype == LQS_C64) return run_adjoint_compiled_t<ArF32>(sv, rev, lam, arith, slot_op, partial, grid);
+  if (arith == LQS_ARITH_F64) return run_adjoint_compiled_t<ArF64>(sv, rev, lam, arith, slot_op, partial, grid);
+  return run_adjoint_compiled_t<ArDF>(sv, rev, lam, arith, slot_op, partial, grid);
 }
 
 int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {

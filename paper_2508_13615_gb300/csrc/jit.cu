@@ -55,6 +55,8 @@ uint32_t host_swz(uint32_t j, int sz) {
   return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
 }
 
+constexpr int kMaxGradSlotsJit = 128;  // gradient slots per compiled adjoint segment
+
 std::string hex(uint64_t x) {
   char b[32];
   std::snprintf(b, sizeof b, "0x%llxull", (unsigned long long)x);
@@ -68,18 +70,22 @@ std::string hex32(uint32_t x) {
 
 class SegGen {
  public:
-  SegGen(int k, int b, int r, const char* aname, int amp_bytes)
-      : k_(k), b_(b), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes) {}
+  // adjoint: the kernel carries psi and lambda (same layout and renamings),
+  // and ops with a gradient slot (and K_GRAD partials) add Im<lambda|G|psi>.
+  SegGen(int k, int b, int r, const char* aname, int amp_bytes, bool adjoint)
+      : k_(k), b_(b), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes), adj_(adjoint) {}
 
   // Returns false (with a reason) for a program this generator does not take.
-  bool run(const TOp* ops, int nops, int ncoef, std::string& src, std::string& kname, std::string& why);
+  bool run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& src, std::string& kname, std::string& why);
 
  private:
   int k_, b_, r_, R_;
   const char* aname_;
   int sz_;
-  int xb_ = 0;        // exchange buffer of the next layout change (they alternate)
-  int next_bar_ = 1;  // next free named barrier id in this tile iteration (0 is the block barrier)
+  bool adj_;
+  const char* pfx_ = "v";       // variables of the state being emitted ("v" psi, "u" lambda)
+  int xb_ = 0;                  // exchange buffer of the next exchange (they alternate)
+  int next_bar_ = 1;            // next free named barrier id in this tile iteration (0 is the block barrier)
   int slot_[4] = {0, 0, 0, 0};  // register slot m -> local position
   int thr_[16] = {0};           // thread bit m -> local position
   int vm_[16];                  // register element -> variable
@@ -88,6 +94,18 @@ class SegGen {
   std::ostringstream pre_;  // before the tile loop (tile-independent per-thread values)
   std::string why_;
 
+  int nthreads() const { return 1 << (k_ - r_); }
+  // runs f once per state, with V() naming that state's variables
+  template <class F>
+  void each(F f) {
+    pfx_ = "v";
+    f();
+    if (adj_) {
+      pfx_ = "u";
+      f();
+    }
+    pfx_ = "v";
+  }
   bool set_layout(uint64_t packed);
   uint32_t je(int e) const {
     uint32_t x = 0;
@@ -106,13 +124,17 @@ class SegGen {
     return x;
   }
   std::string jt_expr() const;
-  std::string V(int e) const { return "v" + std::to_string(vm_[e]); }
+  std::string V(int e) const { return std::string(pfx_) + std::to_string(vm_[e]); }
+  std::string Vs(const char* s, int e) const { return std::string(s) + std::to_string(vm_[e]); }
   std::string cref(int i) const { return "P.coef[" + std::to_string(i) + "]"; }
   std::string fresh(const char* p) { return std::string(p) + std::to_string(uid_++); }
   // predicate of the op's thread-held and outside controls ("" when none),
   // and the register-slot mask its register-held controls require
   std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
+  std::string barrier_for(uint64_t to);
   bool emit_op(const TOp& t);
+  bool emit_grad(const TOp& t);
+  bool emit_grad_block(const TOp* ops, int count);
   void emit_layout(const TOp& t);
   int smem_read_degree() const;
   bool store_friendly() const;
@@ -166,58 +188,78 @@ std::string SegGen::pred(uint32_t lc, uint64_t ec, uint32_t& regc) const {
   return s;
 }
 
-void SegGen::emit_layout(const TOp& t) {
-  // Write the tile in the current layout, read it back in the new one.  The
-  // exchange buffers alternate, so one barrier suffices: the previous reader
-  // of this buffer finished before the intervening exchange's barrier (or
-  // the barriers at the top of the tile loop).
-  const char* X = xb_ ? "XB" : "XA";
-  xb_ ^= 1;
-  // Warp-index thread bits that keep their position confine the exchange to
-  // the warps agreeing on them (each group keeps its set of amplitudes), so
-  // only those warps synchronise: __syncwarp when no warp bit moves, a named
-  // barrier per group when some do, the block barrier when all do.
+// The barrier of one exchange into layout `to`.  Warp-index thread bits that
+// keep their position confine the exchange to the warps agreeing on them
+// (each group keeps its set of amplitudes), so only those warps synchronise:
+// __syncwarp when no warp bit moves, a named barrier per group when some do,
+// the block barrier when all do.  Every group barrier of a tile iteration
+// gets ids of its own: a warp may reach a later exchange while warps of
+// another group are still at an earlier one, and two barrier instances must
+// never share an id.  When the ids run out the block barrier is used; block
+// barriers (here and at the top of the tile loop) make all ids free again.
+std::string SegGen::barrier_for(uint64_t to) {
   uint32_t fixed = 0, moved = 0;
   for (int m = 5; m < k_ - r_; ++m) {
-    const int to = (int)((t.ecmask >> (4 * (r_ + m))) & 15u);
-    if (to == thr_[m]) fixed |= 1u << m;
+    const int q = (int)((to >> (4 * (r_ + m))) & 15u);
+    if (q == thr_[m]) fixed |= 1u << m;
     else moved |= 1u << m;
   }
-  // Every group barrier of a tile iteration gets ids of its own: a warp may
-  // reach a later exchange while warps of another group are still at an
-  // earlier one, and two barrier instances must never share an id.  When the
-  // ids run out the block barrier is used; the block barriers at the top of
-  // the tile loop make all ids free again.
   const int groups = 1 << __builtin_popcount(fixed);
-  std::string bar;
-  if (!moved) {
-    bar = "__syncwarp();";
-  } else if (!fixed || next_bar_ + groups - 1 > 15) {
-    bar = "__syncthreads();";
+  if (!moved) return "__syncwarp();";
+  if (!fixed || next_bar_ + groups - 1 > 15) {
     next_bar_ = 1;  // every warp passes it after all earlier group barriers completed
-  } else {
-    std::string id;
-    int j = 0;
-    for (int m = 5; m < k_ - r_; ++m)
-      if ((fixed >> m) & 1u) {
-        id += " + (((tid >> " + std::to_string(m) + ") & 1u) << " + std::to_string(j) + ")";
-        ++j;
-      }
-    bar = "lqs::jit::bar_group(" + std::to_string(next_bar_) + "u" + id + ", " +
-          std::to_string(32u << __builtin_popcount(moved)) + "u);";
-    next_bar_ += groups;
+    return "__syncthreads();";
   }
-  o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
-  for (int e = 0; e < R_; ++e)
-    o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "], " << V(e) << ");\n";
-  o_ << "    }\n    " << bar << "\n";
-  set_layout(t.ecmask);  // validated by the caller
-  o_ << "    jt = " << jt_expr() << ";\n    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
-  for (int e = 0; e < R_; ++e) {
-    vm_[e] = e;
-    o_ << "      v" << e << " = lqs::ld_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "]);\n";
+  std::string id;
+  int j = 0;
+  for (int m = 5; m < k_ - r_; ++m)
+    if ((fixed >> m) & 1u) {
+      id += " + (((tid >> " + std::to_string(m) + ") & 1u) << " + std::to_string(j) + ")";
+      ++j;
+    }
+  std::string bar = "lqs::jit::bar_group(" + std::to_string(next_bar_) + "u" + id + ", " +
+                    std::to_string(32u << __builtin_popcount(moved)) + "u);";
+  next_bar_ += groups;
+  return bar;
+}
+
+void SegGen::emit_layout(const TOp& t) {
+  // Each state is written in the current layout and read back in the new one
+  // through its own buffer.  The buffers alternate, so one barrier per state
+  // suffices: the previous reader of a buffer finished before the
+  // intervening exchange's barrier (or the barriers at the top of the tile
+  // loop).
+  uint32_t old_je[16];
+  for (int e = 0; e < R_; ++e) old_je[e] = je(e);
+  const int saved_slot[4] = {slot_[0], slot_[1], slot_[2], slot_[3]};
+  int saved_thr[16];
+  std::copy(thr_, thr_ + 16, saved_thr);
+  std::string jo;
+  if (adj_) {
+    jo = fresh("jo");
+    o_ << "    const uint32_t " << jo << " = lqs::jit::swz<" << sz_ << ">(jt);\n";
   }
-  o_ << "    }\n";
+  bool first = true;
+  each([&]() {
+    const char* X = xb_ ? "XB" : "XA";
+    xb_ ^= 1;
+    std::copy(saved_slot, saved_slot + 4, slot_);  // barrier groups compare with the current layout
+    std::copy(saved_thr, saved_thr + 16, thr_);
+    const std::string bar = barrier_for(t.ecmask);
+    if (adj_) o_ << "    { const uint32_t sj = " << jo << ";\n";
+    else o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+    for (int e = 0; e < R_; ++e)
+      o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_swz(old_je[e], sz_)) << "], " << V(e) << ");\n";
+    o_ << "    }\n    " << bar << "\n";
+    set_layout(t.ecmask);  // validated by the caller
+    if (first) o_ << "    jt = " << jt_expr() << ";\n";
+    first = false;
+    o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+    for (int e = 0; e < R_; ++e)
+      o_ << "      " << pfx_ << e << " = lqs::ld_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "]);\n";
+    o_ << "    }\n";
+  });
+  for (int e = 0; e < R_; ++e) vm_[e] = e;
   if (t.e0 != t.ecmask) {  // relabelling SWAPs: from here on amplitudes carry their logical positions
     set_layout(t.e0);
     o_ << "    jt = " << jt_expr() << ";\n";
@@ -264,37 +306,165 @@ void SegGen::emit_store() {
     if (p < b_) pre_ << "  const uint64_t st_" << m << " = " << (1u << p) << "ull;\n";
     else pre_ << "  const uint64_t st_" << m << " = 1ull << G.h[" << (p - b_) << "];\n";
   }
-  o_ << "    { S* out = psi + base + st_t;\n";
-  for (int e = 0; e < R_; ++e) {
-    std::string off;
-    for (int m = 0; m < r_; ++m)
-      if ((e >> m) & 1) off += (off.empty() ? "" : " + ") + ("st_" + std::to_string(m));
-    o_ << "      out[" << (off.empty() ? std::string("0") : off) << "] = A::store(" << V(e) << ");\n";
+  each([&]() {
+    o_ << "    { S* out = " << (pfx_[0] == 'v' ? "psi" : "lam") << " + base + st_t;\n";
+    for (int e = 0; e < R_; ++e) {
+      std::string off;
+      for (int m = 0; m < r_; ++m)
+        if ((e >> m) & 1) off += (off.empty() ? "" : " + ") + ("st_" + std::to_string(m));
+      o_ << "      out[" << (off.empty() ? std::string("0") : off) << "] = A::store(" << V(e) << ");\n";
+    }
+    o_ << "    }\n";
+  });
+}
+
+// Gradient partial of op t (before it is un-applied): Im <lambda|G|psi> over
+// the tile's amplitudes that the op's controls select, for generator G on
+// its target: X, Y (pairs on the target's register slot), Z (a sign per
+// amplitude), or the projector P1 on its control set.  The per-thread sum is
+// reduced over the warp into the warp's float64 slot.
+bool SegGen::emit_grad(const TOp& t) {
+  if (t.gslot < 0) return true;
+  uint32_t regc = 0;
+  const std::string p = pred(t.lcmask, t.ecmask, regc);
+  auto qual = [&](int e) { return ((uint32_t)e & regc) == regc; };
+  const std::string acc = fresh("g");
+  o_ << "    // gradient slot " << t.gslot << "\n    { lqs::jit::GAcc<A>::T " << acc << " = lqs::jit::GAcc<A>::zero();\n";
+  if (!p.empty()) o_ << "      if (" << p << ") {\n";
+  if (t.gen == G_P1 || (t.gen == G_Z && !(t.l0 >= 0 && reg_slot(t.l0) >= 0))) {
+    // single amplitudes; for Z the sign comes from a thread bit or the tile
+    std::string sgn = "false";
+    if (t.gen == G_Z) {
+      if (t.l0 >= 0) sgn = "((jt >> " + std::to_string(t.l0) + ") & 1u) != 0u";
+      else if (t.e0) sgn = "(base & " + hex(t.e0) + ") != 0ull";
+      else return fail("Z generator without a target");
+    }
+    for (int e = 0; e < R_; ++e)
+      if (qual(e)) o_ << "        lqs::jit::gim<A>(" << acc << ", " << Vs("u", e) << ", " << Vs("v", e) << ", " << sgn << ");\n";
+  } else {
+    const int m = t.l0 >= 0 ? reg_slot(t.l0) : -1;
+    if (m < 0 || (t.gen != G_X && t.gen != G_Y && t.gen != G_Z)) return fail("generator target not in a register slot");
+    for (int e = 0; e < R_; ++e) {
+      if ((e >> m) & 1 || !qual(e)) continue;
+      const int a = e, b = e | (1 << m);
+      if (t.gen == G_X) {  // conj(l0) p1 + conj(l1) p0
+        o_ << "        lqs::jit::gim<A>(" << acc << ", " << Vs("u", a) << ", " << Vs("v", b) << ", false);\n";
+        o_ << "        lqs::jit::gim<A>(" << acc << ", " << Vs("u", b) << ", " << Vs("v", a) << ", false);\n";
+      } else if (t.gen == G_Y) {  // conj(l0)(-i p1) + conj(l1)(i p0)
+        o_ << "        lqs::jit::gre<A>(" << acc << ", " << Vs("u", a) << ", " << Vs("v", b) << ", true);\n";
+        o_ << "        lqs::jit::gre<A>(" << acc << ", " << Vs("u", b) << ", " << Vs("v", a) << ", false);\n";
+      } else {  // Z: conj(l0) p0 - conj(l1) p1
+        o_ << "        lqs::jit::gim<A>(" << acc << ", " << Vs("u", a) << ", " << Vs("v", a) << ", false);\n";
+        o_ << "        lqs::jit::gim<A>(" << acc << ", " << Vs("u", b) << ", " << Vs("v", b) << ", true);\n";
+      }
+    }
+  }
+  if (!p.empty()) o_ << "      }\n";
+  o_ << "      lqs::jit::gflush(" << acc << ", wacc + warp * " << kMaxGradSlotsJit << " + " << t.gslot << ");\n    }\n";
+  return true;
+}
+
+// Gradient partials of the Z / P1 generators of a merged diagonal run (the
+// consecutive K_GRAD ops before it): each is a signed sum of the same terms
+// w_j = Im(conj(lambda_j) psi_j), so the terms are formed once per amplitude
+// and the sums once per pattern (register-held controls, sign slot); the
+// thread- or tile-dependent sign and predicate are applied per op.
+bool SegGen::emit_grad_block(const TOp* ops, int count) {
+  o_ << "    { // gradient partials of a merged diagonal run\n";
+  const std::string wn = fresh("w");
+  for (int e = 0; e < R_; ++e)
+    o_ << "      const lqs::jit::GAcc<A>::V " << wn << "_" << e << " = lqs::jit::wim<A>(" << Vs("u", e) << ", "
+       << Vs("v", e) << ");\n";
+  std::map<std::pair<uint32_t, int>, std::string> sums, walsh;
+  for (int i = 0; i < count; ++i) {
+    const TOp& t = ops[i];
+    if (t.kind != K_GRAD || (t.gen != G_Z && t.gen != G_P1)) return fail("internal: unexpected op in a gradient block");
+    uint32_t regc = 0;
+    // register-held controls select elements; thread-held ones make a per-lane
+    // predicate; outside ones a per-tile one
+    uint32_t thc = 0;
+    for (int p = 0; p < k_; ++p)
+      if (((t.lcmask >> p) & 1u) && reg_slot(p) < 0) thc |= 1u << p;
+    const std::string p = pred(t.lcmask, 0, regc);
+    const std::string tp = t.ecmask ? "((base & " + hex(t.ecmask) + ") == " + hex(t.ecmask) + ")" : "true";
+    int sm = -1;      // register slot giving the sign, for Z on a register-held target
+    int lbit = -1;    // lane bit giving the sign
+    std::string rs;   // uniform sign (warp bit or qubit outside the tile)
+    if (t.gen == G_Z) {
+      if (t.l0 >= 0 && reg_slot(t.l0) >= 0) {
+        sm = reg_slot(t.l0);
+      } else if (t.l0 >= 0) {
+        int m = 0;
+        while (m < k_ - r_ && thr_[m] != t.l0) ++m;
+        if (m == k_ - r_) return fail("Z target neither in registers nor on a thread bit");
+        if (m < 5) lbit = m;
+        else rs = "((tid >> " + std::to_string(m) + ") & 1u) != 0u";
+      } else if (t.e0) {
+        rs = "(base & " + hex(t.e0) + ") != 0ull";
+      } else {
+        return fail("Z generator without a target");
+      }
+    }
+    const auto key = std::make_pair(regc, sm);
+    auto it = sums.find(key);
+    if (it == sums.end()) {
+      const std::string sn = fresh("s");
+      o_ << "      lqs::jit::GAcc<A>::T " << sn << " = lqs::jit::GAcc<A>::zero();\n";
+      for (int e = 0; e < R_; ++e)
+        if (((uint32_t)e & regc) == regc)
+          o_ << "      lqs::jit::wadd(" << sn << ", " << wn << "_" << e << ", " << ((sm >= 0 && ((e >> sm) & 1)) ? "true" : "false")
+             << ");\n";
+      it = sums.emplace(key, sn).first;
+    }
+    const std::string slot = "wacc + warp * " + std::to_string(kMaxGradSlotsJit) + " + " + std::to_string(t.gslot);
+    if (thc) {  // a per-lane predicate: this partial needs its own warp sum
+      std::string val = rs.empty() ? it->second : "lqs::jit::gneg(" + it->second + ", " + rs + ")";
+      val = "(" + p + " && " + tp + ") ? " + val + " : lqs::jit::GAcc<A>::zero()";
+      if (lbit >= 0) val = "lqs::jit::gneg(" + val + ", ((tid >> " + std::to_string(lbit) + ") & 1u) != 0u)";
+      o_ << "      lqs::jit::gflush(" << val << ", " << slot << ");  // gradient slot " << t.gslot << "\n";
+      continue;
+    }
+    // one Walsh butterfly per pattern serves every partial that uses it
+    auto wt = walsh.find(key);
+    if (wt == walsh.end()) {
+      const std::string wv = fresh("W");
+      o_ << "      const auto " << wv << " = lqs::jit::wht(" << it->second << ");\n";
+      wt = walsh.emplace(key, wv).first;
+    }
+    const std::string lane = "(tid & 31u) == " + std::to_string(lbit >= 0 ? (1u << lbit) : 0u);
+    o_ << "      lqs::jit::gput(" << wt->second << ", " << lane << " && " << tp << ", " << (rs.empty() ? "false" : rs)
+       << ", " << slot << ");  // gradient slot " << t.gslot << "\n";
   }
   o_ << "    }\n";
+  return true;
 }
 
 bool SegGen::emit_op(const TOp& t) {
   uint32_t regc = 0;
   const int c = t.coef;
   auto qual = [&](int e) { return ((uint32_t)e & regc) == regc; };
+  if (adj_ && !emit_grad(t)) return false;
   switch (t.kind) {
     case K_LAYOUT:
       return fail("internal: layout reached emit_op");
+    case K_GRAD:
+      return adj_ ? true : fail("gradient partial outside an adjoint program");
     case K_PHASE: {
       const std::string p = pred(t.lcmask, t.ecmask, regc);
       o_ << "    // phase\n";
       if (!p.empty()) o_ << "    if (" << p << ") {\n";
-      for (int e = 0; e < R_; ++e) {
-        if (!qual(e)) continue;
-        const std::string v = V(e);
-        switch (t.special) {
-          case 1: o_ << "      " << v << " = A::neg(" << v << ");\n"; break;
-          case 2: o_ << "      " << v << " = A::mul_i(" << v << ");\n"; break;
-          case 3: o_ << "      " << v << " = A::neg(A::mul_i(" << v << "));\n"; break;
-          default: o_ << "      " << v << " = A::cmul(" << cref(c) << ", " << v << ");\n"; break;
+      each([&]() {
+        for (int e = 0; e < R_; ++e) {
+          if (!qual(e)) continue;
+          const std::string v = V(e);
+          switch (t.special) {
+            case 1: o_ << "      " << v << " = A::neg(" << v << ");\n"; break;
+            case 2: o_ << "      " << v << " = A::mul_i(" << v << ");\n"; break;
+            case 3: o_ << "      " << v << " = A::neg(A::mul_i(" << v << "));\n"; break;
+            default: o_ << "      " << v << " = A::cmul(" << cref(c) << ", " << v << ");\n"; break;
+          }
         }
-      }
+      });
       if (!p.empty()) o_ << "    }\n";
       return true;
     }
@@ -304,15 +474,19 @@ bool SegGen::emit_op(const TOp& t) {
       if (!p.empty()) o_ << "    if (" << p << ") {\n";
       const int m = t.l0 >= 0 ? reg_slot(t.l0) : -1;
       if (m >= 0) {
-        for (int e = 0; e < R_; ++e)
-          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << cref(c + ((e >> m) & 1)) << ", " << V(e) << ");\n";
+        each([&]() {
+          for (int e = 0; e < R_; ++e)
+            if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << cref(c + ((e >> m) & 1)) << ", " << V(e) << ");\n";
+        });
       } else {
         const std::string d = fresh("d");
         const std::string bit = t.l0 >= 0 ? "((jt >> " + std::to_string(t.l0) + ") & 1u)"
                                           : "((base & " + hex(t.e0) + ") != 0ull)";
         o_ << "      const C " << d << " = " << bit << " ? " << cref(c + 1) << " : " << cref(c) << ";\n";
-        for (int e = 0; e < R_; ++e)
-          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << d << ", " << V(e) << ");\n";
+        each([&]() {
+          for (int e = 0; e < R_; ++e)
+            if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << d << ", " << V(e) << ");\n";
+        });
       }
       if (!p.empty()) o_ << "    }\n";
       return true;
@@ -327,31 +501,34 @@ bool SegGen::emit_op(const TOp& t) {
         return l >= 0 ? "((jt >> " + std::to_string(l) + ") & 1u)" : "((base & " + hex(em) + ") != 0ull)";
       };
       const std::string r0 = rbit(t.l0, t.e0), r1 = rbit(t.l1, t.e1);
+      std::vector<std::string> fac(R_);
       std::map<int, std::string> sel;  // compile-time pattern -> coefficient expression
       for (int e = 0; e < R_; ++e) {
         if (!qual(e)) continue;
         const int b0 = m0 >= 0 ? (e >> m0) & 1 : -1, b1 = m1 >= 0 ? (e >> m1) & 1 : -1;
-        std::string f;
         if (b0 >= 0 && b1 >= 0) {
-          f = cref(c + 2 * b0 + b1);
-        } else {
-          const int key = (b0 + 1) * 3 + (b1 + 1);
-          auto it = sel.find(key);
-          if (it == sel.end()) {
-            std::string ex;
-            if (b0 < 0 && b1 >= 0) ex = r0 + " ? " + cref(c + 2 + b1) + " : " + cref(c + b1);
-            else if (b0 >= 0 && b1 < 0) ex = r1 + " ? " + cref(c + 2 * b0 + 1) + " : " + cref(c + 2 * b0);
-            else
-              ex = r0 + " ? (" + r1 + " ? " + cref(c + 3) + " : " + cref(c + 2) + ") : (" + r1 + " ? " + cref(c + 1) +
-                   " : " + cref(c) + ")";
-            const std::string d = fresh("d");
-            o_ << "      const C " << d << " = " << ex << ";\n";
-            it = sel.emplace(key, d).first;
-          }
-          f = it->second;
+          fac[e] = cref(c + 2 * b0 + b1);
+          continue;
         }
-        o_ << "      " << V(e) << " = A::cmul(" << f << ", " << V(e) << ");\n";
+        const int key = (b0 + 1) * 3 + (b1 + 1);
+        auto it = sel.find(key);
+        if (it == sel.end()) {
+          std::string ex;
+          if (b0 < 0 && b1 >= 0) ex = r0 + " ? " + cref(c + 2 + b1) + " : " + cref(c + b1);
+          else if (b0 >= 0 && b1 < 0) ex = r1 + " ? " + cref(c + 2 * b0 + 1) + " : " + cref(c + 2 * b0);
+          else
+            ex = r0 + " ? (" + r1 + " ? " + cref(c + 3) + " : " + cref(c + 2) + ") : (" + r1 + " ? " + cref(c + 1) +
+                 " : " + cref(c) + ")";
+          const std::string d = fresh("d");
+          o_ << "      const C " << d << " = " << ex << ";\n";
+          it = sel.emplace(key, d).first;
+        }
+        fac[e] = it->second;
       }
+      each([&]() {
+        for (int e = 0; e < R_; ++e)
+          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << fac[e] << ", " << V(e) << ");\n";
+      });
       if (!p.empty()) o_ << "    }\n";
       return true;
     }
@@ -373,32 +550,39 @@ bool SegGen::emit_op(const TOp& t) {
       if (plain) {
         const std::string q = fresh("p");
         o_ << "    { const bool " << q << " = " << p << ";\n";
-        for (int e = 0; e < R_; ++e)
-          if (!((e >> m) & 1) && qual(e))
-            o_ << "      lqs::jit::swap_if(" << q << ", " << V(e) << ", " << V(e | (1 << m)) << ");\n";
+        each([&]() {
+          for (int e = 0; e < R_; ++e)
+            if (!((e >> m) & 1) && qual(e))
+              o_ << "      lqs::jit::swap_if(" << q << ", " << V(e) << ", " << V(e | (1 << m)) << ");\n";
+        });
         o_ << "    }\n";
         return true;
       }
       if (t.kind == K_ANTI1 && p.empty()) {  // (a, b) <- (f0 b, f1 a): scale in place, then rename
-        for (int e = 0; e < R_; ++e) {
-          if ((e >> m) & 1 || !qual(e)) continue;
-          const int a = e, b = e | (1 << m);
-          o_ << "    " << V(b) << " = A::cmul(" << cref(c) << ", " << V(b) << ");\n";
-          o_ << "    " << V(a) << " = A::cmul(" << cref(c + 1) << ", " << V(a) << ");\n";
-          std::swap(vm_[a], vm_[b]);
-        }
+        each([&]() {
+          for (int e = 0; e < R_; ++e) {
+            if ((e >> m) & 1 || !qual(e)) continue;
+            const int a = e, b = e | (1 << m);
+            o_ << "    " << V(b) << " = A::cmul(" << cref(c) << ", " << V(b) << ");\n";
+            o_ << "    " << V(a) << " = A::cmul(" << cref(c + 1) << ", " << V(a) << ");\n";
+          }
+        });
+        for (int e = 0; e < R_; ++e)
+          if (!((e >> m) & 1) && qual(e)) std::swap(vm_[e], vm_[e | (1 << m)]);
         return true;
       }
       if (!p.empty()) o_ << "    if (" << p << ") {\n";
-      for (int e = 0; e < R_; ++e) {
-        if ((e >> m) & 1 || !qual(e)) continue;
-        const std::string a = V(e), b = V(e | (1 << m));
-        if (t.kind == K_ANTI1)
-          o_ << "      lqs::jit::anti<A>(" << a << ", " << b << ", " << cref(c) << ", " << cref(c + 1) << ");\n";
-        else
-          o_ << "      lqs::jit::" << (t.kind == K_DENSE1 ? "d1" : "d1r") << "<A>(" << a << ", " << b << ", "
-             << cref(c) << ", " << cref(c + 1) << ", " << cref(c + 2) << ", " << cref(c + 3) << ");\n";
-      }
+      each([&]() {
+        for (int e = 0; e < R_; ++e) {
+          if ((e >> m) & 1 || !qual(e)) continue;
+          const std::string a = V(e), b = V(e | (1 << m));
+          if (t.kind == K_ANTI1)
+            o_ << "      lqs::jit::anti<A>(" << a << ", " << b << ", " << cref(c) << ", " << cref(c + 1) << ");\n";
+          else
+            o_ << "      lqs::jit::" << (t.kind == K_DENSE1 ? "d1" : "d1r") << "<A>(" << a << ", " << b << ", "
+               << cref(c) << ", " << cref(c + 1) << ", " << cref(c + 2) << ", " << cref(c + 3) << ");\n";
+        }
+      });
       if (!p.empty()) o_ << "    }\n";
       return true;
     }
@@ -419,19 +603,23 @@ bool SegGen::emit_op(const TOp& t) {
         }
         const std::string q = fresh("p");
         o_ << "    { const bool " << q << " = " << p << ";\n";
-        for (int e = 0; e < R_; ++e)
-          if (!(e & A_) && !(e & B_) && qual(e))
-            o_ << "      lqs::jit::swap_if(" << q << ", " << V(e | A_) << ", " << V(e | B_) << ");\n";
+        each([&]() {
+          for (int e = 0; e < R_; ++e)
+            if (!(e & A_) && !(e & B_) && qual(e))
+              o_ << "      lqs::jit::swap_if(" << q << ", " << V(e | A_) << ", " << V(e | B_) << ");\n";
+        });
         o_ << "    }\n";
         return true;
       }
       if (!p.empty()) o_ << "    if (" << p << ") {\n";
-      for (int e = 0; e < R_; ++e) {
-        if ((e & A_) || (e & B_) || !qual(e)) continue;
-        // amplitude order 2 * bit(t0) + bit(t1)
-        o_ << "      lqs::jit::d2<A>(" << V(e) << ", " << V(e | B_) << ", " << V(e | A_) << ", " << V(e | A_ | B_)
-           << ", &" << cref(c) << ");\n";
-      }
+      each([&]() {
+        for (int e = 0; e < R_; ++e) {
+          if ((e & A_) || (e & B_) || !qual(e)) continue;
+          // amplitude order 2 * bit(t0) + bit(t1)
+          o_ << "      lqs::jit::d2<A>(" << V(e) << ", " << V(e | B_) << ", " << V(e | A_) << ", " << V(e | A_ | B_)
+             << ", &" << cref(c) << ");\n";
+        }
+      });
       if (!p.empty()) o_ << "    }\n";
       return true;
     }
@@ -489,8 +677,10 @@ bool SegGen::emit_op(const TOp& t) {
         o_ << "      const C " << nm << " = A::kmul(" << cref(lidx(slot_[m])) << ", " << tab[key ^ (1u << m)] << ");\n";
         tab[key] = nm;
       }
-      for (int e = 0; e < R_; ++e)
-        if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << tab[(uint32_t)e & fmask] << ", " << V(e) << ");\n";
+      each([&]() {
+        for (int e = 0; e < R_; ++e)
+          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << tab[(uint32_t)e & fmask] << ", " << V(e) << ");\n";
+      });
       o_ << "    }\n";
       if (!p.empty()) o_ << "    }\n";
       return true;
@@ -501,27 +691,35 @@ bool SegGen::emit_op(const TOp& t) {
 }
 
 const char* kSkeletonHead = R"(
-extern "C" __global__ void __launch_bounds__(256, 2)
-@NAME@(A::S* __restrict__ psi, const __grid_constant__ SegArgs P, int* status) {
+extern "C" __global__ void __launch_bounds__(@NTH@, @MINB@)
+@NAME@(A::S* __restrict__ psi, @LAMP@const __grid_constant__ SegArgs P, @PARTP@int* status) {
   typedef A::S S;
   typedef A::W W;
   typedef A::C C;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const lqs::TileGeom& G = P.g;
   S* S0 = reinterpret_cast<S*>(smem_raw);  // incoming tiles (bulk loads, prefetched one tile ahead)
-  W* XA = reinterpret_cast<W*>(S0 + @NT@);  // layout exchanges alternate between XA and XB
+  S* S0L = S0 + @NT@;                      // incoming lambda tiles (adjoint only)
+  W* XA = reinterpret_cast<W*>(S0 + @NT@ * @NIN@);  // layout exchanges alternate between XA and XB
   W* XB = XA + @NT@;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(XB + @NT@);
+  double* wacc = reinterpret_cast<double*>(XB + @NT@);  // adjoint: per-warp gradient slots
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wacc + @NWACC@);
   const uint32_t tid = threadIdx.x;
+  const uint32_t warp = tid >> 5;
+  (void)S0L;
+  (void)warp;
+  for (uint32_t i = tid; i < @NWACC@; i += blockDim.x) wacc[i] = 0.0;
   uint64_t t = blockIdx.x;
   if (tid == 0) {
     lqs::mbar_init(bar, 1);
     lqs::fence_mbar_init();
-    if (t < G.ntiles) lqs::jit::seg_expect(G, bar);
+    if (t < G.ntiles) lqs::jit::seg_expect(G, bar, @NSTATES@);
   }
   __syncthreads();
   const uint64_t my_roff = tid < (1u << G.r) ? lqs::row_offset(G, tid) : 0ull;
-  if (t < G.ntiles) lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, t), bar, my_roff);
+  if (t < G.ntiles) {
+    lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, t), bar, my_roff);
+@LAMCOPY0@  }
   uint32_t phase = 0;
   bool ok = true;
 @PRE@  for (; t < G.ntiles; t += gridDim.x) {
@@ -530,7 +728,7 @@ extern "C" __global__ void __launch_bounds__(256, 2)
     phase ^= 1u;
     if (!ok) break;
     // the next phase's byte count goes up before any of its copies is issued
-    if (tid == 0 && t + gridDim.x < G.ntiles) lqs::jit::seg_expect(G, bar);
+    if (tid == 0 && t + gridDim.x < G.ntiles) lqs::jit::seg_expect(G, bar, @NSTATES@);
 )";
 
 const char* kSkeletonTail = R"(  }
@@ -538,7 +736,15 @@ const char* kSkeletonTail = R"(  }
     lqs::flag_timeout(status, 4);
     lqs::mbar_wait(bar, phase ^ 1u);
   }
-}
+@GRADOUT@}
+)";
+
+const char* kGradOut = R"(  __syncthreads();
+  for (int s = tid; s < @NGRAD@; s += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < @NWARPS@; ++w) v += wacc[w * @SLOTS@ + s];
+    partial[(size_t)s * gridDim.x + blockIdx.x] = v;
+  }
 )";
 
 std::string replace_all(std::string s, const std::string& a, const std::string& b) {
@@ -555,9 +761,14 @@ uint64_t fnv1a(const std::string& s) {
   return h;
 }
 
-bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::string& kname, std::string& why) {
+bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& src, std::string& kname,
+                 std::string& why) {
   if (nops < 1 || ops[0].kind != K_LAYOUT) {
     why = "program does not start with a layout";
+    return false;
+  }
+  if (ngrad > kMaxGradSlotsJit) {
+    why = "too many gradient slots";
     return false;
   }
   for (int i = 0; i < nops; ++i)
@@ -584,17 +795,24 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::str
   set_layout(through);
   for (int e = 0; e < R_; ++e) vm_[e] = e;
   o_ << "    uint32_t jt = " << jt_expr() << ";\n";
-  o_ << "    W";
-  for (int e = 0; e < R_; ++e) o_ << (e ? ", v" : " v") << e;
-  o_ << ";\n";
-  for (int e = 0; e < R_; ++e) o_ << "    v" << e << " = A::load(S0[jt + " << hex32(je(e)) << "]);\n";
+  each([&]() {
+    o_ << "    W";
+    for (int e = 0; e < R_; ++e) o_ << (e ? ", " : " ") << pfx_ << e;
+    o_ << ";\n";
+    for (int e = 0; e < R_; ++e)
+      o_ << "    " << pfx_ << e << " = A::load(" << (pfx_[0] == 'v' ? "S0" : "S0L") << "[jt + " << hex32(je(e))
+         << "]);\n";
+  });
   if (logical != through) {
     set_layout(logical);
     o_ << "    jt = " << jt_expr() << ";\n";
   }
-  o_ << "    __syncthreads();  // the incoming buffer is free: prefetch the next tile into it\n"
+  o_ << "    __syncthreads();  // the incoming buffers are free: prefetch the next tile into them\n"
         "    { const uint64_t tn = t + gridDim.x;\n"
-        "      if (tn < G.ntiles) lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, tn), bar, my_roff); }\n";
+        "      if (tn < G.ntiles) {\n"
+        "        lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, tn), bar, my_roff);\n";
+  if (adj_) o_ << "        lqs::jit::seg_copy(G, S0L, lam, lqs::tile_base(G, tn), bar, my_roff);\n";
+  o_ << "      } }\n";
   for (int i = first; i < nops; ++i) {
     if (ops[i].kind == K_LAYOUT) {
       if (i == nops - 1) {
@@ -617,6 +835,16 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::str
       emit_layout(ops[i]);
       continue;
     }
+    if (adj_ && ops[i].kind == K_GRAD) {
+      int j = i;
+      while (j < nops && ops[j].kind == K_GRAD) ++j;
+      if (!emit_grad_block(ops + i, j - i)) {
+        why = why_;
+        return false;
+      }
+      i = j - 1;
+      continue;
+    }
     if (!emit_op(ops[i])) {
       why = why_;
       return false;
@@ -625,21 +853,44 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, std::string& src, std::str
   emit_store();  // natural order, or a layout that keeps sectors on lanes
   const std::string body = o_.str();
   const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^
-                     ((uint64_t)b_ << 36) ^ fnv1a(aname_);
+                     ((uint64_t)b_ << 36) ^ ((uint64_t)ngrad << 24) ^ (adj_ ? 0x5a5aull : 0ull) ^ fnv1a(aname_);
   char nm[40];
-  std::snprintf(nm, sizeof nm, "lqs_seg_%016llx", (unsigned long long)h);
+  std::snprintf(nm, sizeof nm, adj_ ? "lqs_adj_%016llx" : "lqs_seg_%016llx", (unsigned long long)h);
   kname = nm;
+  const int nth = nthreads(), nwarps = nth / 32;
   std::ostringstream s;
-  s << "// compiled fused segment: " << nops << " ops, " << ncoef << " coefficients\n"
+  s << "// compiled " << (adj_ ? "adjoint" : "fused") << " segment: " << nops << " ops, " << ncoef
+    << " coefficients, " << ngrad << " gradient slots\n"
     << "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
        "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n"
     << "#include \"tile.cuh\"\n#include \"jit_dev.cuh\"\n"
     << "typedef " << aname_ << " A;\n"
     << "struct SegArgs {\n  lqs::TileGeom g;\n  A::C coef[" << std::max(ncoef, 1) << "];\n};\n";
   std::string head = replace_all(kSkeletonHead, "@NAME@", kname);
+  head = replace_all(head, "@NTH@", std::to_string(nth));
+  // resident CTAs per SM the register budget aims at: forward 2 x 256
+  // threads; adjoint 3 x 128, or with 256 threads 2 (4 amplitudes of each
+  // state per thread) or 1 (8 or more)
+  const int minb = !adj_ ? std::max(1, 512 / nth) : nth <= 128 ? 3 : (R_ * sz_ <= 64 ? 2 : 1);
+  head = replace_all(head, "@MINB@", std::to_string(minb));
+  head = replace_all(head, "@LAMP@", adj_ ? "A::S* __restrict__ lam, " : "");
+  head = replace_all(head, "@PARTP@", adj_ ? "double* partial, " : "");
   head = replace_all(head, "@NT@", std::to_string(1u << k_) + "u");
+  head = replace_all(head, "@NIN@", adj_ ? "2u" : "1u");
+  head = replace_all(head, "@NSTATES@", adj_ ? "2u" : "1u");
+  head = replace_all(head, "@NWACC@", std::to_string(adj_ ? nwarps * kMaxGradSlotsJit : 0) + "u");
+  head = replace_all(head, "@LAMCOPY0@",
+                     adj_ ? "    lqs::jit::seg_copy(G, S0L, lam, lqs::tile_base(G, t), bar, my_roff);\n" : "");
   head = replace_all(head, "@PRE@", pre_.str());
-  s << head << body << kSkeletonTail;
+  std::string tail = kSkeletonTail;
+  std::string gout;
+  if (adj_) {
+    gout = replace_all(kGradOut, "@NGRAD@", std::to_string(ngrad));
+    gout = replace_all(gout, "@NWARPS@", std::to_string(nwarps));
+    gout = replace_all(gout, "@SLOTS@", std::to_string(kMaxGradSlotsJit));
+  }
+  tail = replace_all(tail, "@GRADOUT@", gout);
+  s << head << body << tail;
   src = s.str();
   return true;
 }
@@ -802,9 +1053,14 @@ bool wants_compile(const Entry& e, int n) {
 
 // Compiles one entry (no lock held: NVRTC programs are independent).
 void compile_entry(Entry* e) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (e->state != 0) return;  // compiled (or rejected) already
+  }
   const auto t0 = std::chrono::steady_clock::now();
-  if (const char* dir = std::getenv("LQS_JIT_DUMP")) {  // keep the generated source for inspection
-    if (FILE* f = std::fopen((std::string(dir) + "/" + e->name + ".cu").c_str(), "w")) {
+  const char* dump = std::getenv("LQS_JIT_DUMP");  // keep the generated source and compile log
+  if (dump) {
+    if (FILE* f = std::fopen((std::string(dump) + "/" + e->name + ".cu").c_str(), "w")) {
       std::fwrite(e->src.data(), 1, e->src.size(), f);
       std::fclose(f);
     }
@@ -816,8 +1072,8 @@ void compile_entry(Entry* e) {
   bool ok = false;
   if (N.create(&prog, e->src.c_str(), (e->name + ".cu").c_str(), kJitHeaderCount, kJitHeaderSources,
                kJitHeaderNames) == NVRTC_SUCCESS) {
-    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
-    const nvrtcResult r = N.compile(prog, 4, opts);
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG", "--ptxas-options=-v"};
+    const nvrtcResult r = N.compile(prog, dump ? 5 : 4, opts);
     size_t ls = 0;
     if (N.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
       log.resize(ls);
@@ -833,6 +1089,12 @@ void compile_entry(Entry* e) {
     N.destroy(&prog);
   } else {
     log = "nvrtcCreateProgram failed";
+  }
+  if (dump && !log.empty()) {  // with the dump: ptxas's register, spill and shared-memory report
+    if (FILE* f = std::fopen((std::string(dump) + "/" + e->name + ".log").c_str(), "w")) {
+      std::fwrite(log.data(), 1, log.size(), f);
+      std::fclose(f);
+    }
   }
   const auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
   g_compile_us += (uint64_t)us;
@@ -861,6 +1123,44 @@ void compile_all(const std::vector<Entry*>& todo) {
   for (auto& t : th) t.join();
 }
 
+// Structure key of a program: every field the generated source depends on
+// (geometry shape, arithmetic, op fields, coefficient and gradient slot
+// indices; not the coefficient values), so the source is generated only the
+// first time a structure is met.
+std::unordered_map<std::string, Entry*> g_keys;
+
+template <class A>
+std::string struct_key(const TileProg<A>& P, int r, bool adjoint, const char* aname) {
+  std::string k;
+  k.reserve(32 + (size_t)P.nops * 48);
+  auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+  const int hdr[6] = {P.g.k, P.g.b, r, P.ncoef, adjoint ? P.ngrad : -1, P.nops};
+  put(hdr, sizeof hdr);
+  k += aname;
+  for (int i = 0; i < P.nops; ++i) {
+    const TOp& t = P.op[i];
+    const uint8_t b8[4] = {t.kind, t.special, t.gen, 0};
+    const int8_t s8[4] = {t.l0, t.l1, t.s0, t.s1};
+    const int16_t s16[2] = {t.coef, t.gslot};
+    put(b8, 4);
+    put(s8, 4);
+    put(s16, 4);
+    put(&t.lcmask, 4);
+    put(&t.ecmask, 8);
+    put(&t.e0, 8);
+    put(&t.e1, 8);
+  }
+  return k;
+}
+
+Entry* find_key(const std::string& key, bool count_use) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_keys.find(key);
+  if (it == g_keys.end()) return nullptr;
+  if (count_use) ++it->second->uses;
+  return it->second;
+}
+
 Entry* find_or_add(const std::string& src, const std::string& name, bool count_use) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(src);
@@ -883,9 +1183,30 @@ template <> struct JitTypeName<ArF64> { static constexpr const char* s = "lqs::A
 template <> struct JitTypeName<ArDF> { static constexpr const char* s = "lqs::ArDF"; };
 
 template <class A>
-int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why) {
-  SegGen g(P.g.k, P.g.b, r, JitTypeName<A>::s, A::kAmpBytes);
-  return g.run(P.op, P.nops, P.ncoef, src, name, why) ? LQS_OK : LQS_ERR_UNSUPPORTED;
+int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why, bool adjoint) {
+  SegGen g(P.g.k, P.g.b, r, JitTypeName<A>::s, A::kAmpBytes, adjoint);
+  return g.run(P.op, P.nops, P.ncoef, adjoint ? P.ngrad : 0, src, name, why) ? LQS_OK : LQS_ERR_UNSUPPORTED;
+}
+
+// The cache entry of a program's structure (nullptr when the generator does
+// not take it or the cache is full).
+template <class A>
+static Entry* entry_for(const TileProg<A>& P, int r, bool adjoint, bool count_use, std::string* why) {
+  const std::string key = struct_key(P, r, adjoint, JitTypeName<A>::s);
+  if (Entry* e = find_key(key, count_use)) return e;
+  std::string src, name, w;
+  if (jit_source(P, r, src, name, w, adjoint) != LQS_OK) {
+    if (why) *why = w;
+    return nullptr;
+  }
+  Entry* e = find_or_add(src, name, count_use);
+  if (!e) {
+    if (why) *why = "compiled-kernel cache is full";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_keys.emplace(key, e);
+  return e;
 }
 
 int jit_mode() { return mode_now(); }
@@ -897,10 +1218,8 @@ bool jit_enabled_for(int n) {
 
 template <class A>
 int jit_note(const TileProg<A>& P, int r, int n, bool force, std::vector<void*>& todo) {
-  std::string src, name, why;
-  if (jit_source(P, r, src, name, why) != LQS_OK) return LQS_OK;  // the interpreter runs it
-  Entry* e = find_or_add(src, name, true);
-  if (!e) return LQS_OK;
+  Entry* e = entry_for(P, r, false, true, nullptr);
+  if (!e) return LQS_OK;  // the interpreter runs it
   if (e->state == 0 && (force || wants_compile(*e, n)) &&
       std::find(todo.begin(), todo.end(), (void*)e) == todo.end())
     todo.push_back(e);
@@ -937,55 +1256,64 @@ int jit_states(const std::vector<void*>& todo, int* ok, std::string* err) {
   return bad ? LQS_ERR_UNSUPPORTED : LQS_OK;
 }
 
-template <class A>
-int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, const char* prof_name,
-               bool* launched) {
-  *launched = false;
-  if (!jit_enabled_for(sv->n)) return LQS_OK;
-  std::string src, name, why;
-  if (jit_source(P, r, src, name, why) != LQS_OK) return LQS_OK;
-  Entry* e = find_or_add(src, name, false);
-  if (!e || e->state != 1) return LQS_OK;
-  const int dev = sv->device;
-  if (dev < 0 || dev >= kJitMaxDevices) return LQS_OK;
-  const size_t smem = 3 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;  // incoming tile, two exchange buffers
-  CUfunction fn;
-  int per_sm;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!e->fn[dev]) {
-      if (!load_driver()) return set_error(LQS_ERR_UNSUPPORTED, g_drv.err);
-      LQS_CUDA_TRY(cudaSetDevice(dev));  // makes the device's primary context current on this thread
-      CUmodule mod;
-      CUresult rr = g_drv.load(&mod, e->cubin.data());
-      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuModuleLoadData(compiled segment)");
-      CUfunction f;
-      rr = g_drv.get_function(&f, mod, e->name.c_str());
-      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuModuleGetFunction(compiled segment)");
-      rr = g_drv.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem);
-      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuFuncSetAttribute(compiled segment)");
-      int ps = 0;
-      rr = g_drv.occupancy(&ps, f, kTileThreads, smem);
-      if (rr != CUDA_SUCCESS) return cu_error(rr, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
-      e->per_sm[dev] = std::max(ps, 1);
-      e->fn[dev] = f;
-    }
-    fn = e->fn[dev];
-    per_sm = e->per_sm[dev];
+// The kernel of a compiled entry on device `dev` (loaded on first use).
+static int entry_function(Entry* e, int dev, size_t smem, int threads, CUfunction* fn, int* per_sm) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!e->fn[dev]) {
+    if (!load_driver()) return set_error(LQS_ERR_UNSUPPORTED, g_drv.err);
+    LQS_CUDA_TRY(cudaSetDevice(dev));  // makes the device's primary context current on this thread
+    CUmodule mod;
+    CUresult rr = g_drv.load(&mod, e->cubin.data());
+    if (rr != CUDA_SUCCESS) return cu_error(rr, "cuModuleLoadData(compiled segment)");
+    CUfunction f;
+    rr = g_drv.get_function(&f, mod, e->name.c_str());
+    if (rr != CUDA_SUCCESS) return cu_error(rr, "cuModuleGetFunction(compiled segment)");
+    rr = g_drv.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem);
+    if (rr != CUDA_SUCCESS) return cu_error(rr, "cuFuncSetAttribute(compiled segment)");
+    int ps = 0;
+    rr = g_drv.occupancy(&ps, f, threads, smem);
+    if (rr != CUDA_SUCCESS) return cu_error(rr, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+    e->per_sm[dev] = std::max(ps, 1);
+    e->fn[dev] = f;
   }
-  // kernel parameters: the tile geometry, then the used coefficients
+  *fn = e->fn[dev];
+  *per_sm = e->per_sm[dev];
+  return LQS_OK;
+}
+
+// Kernel parameter block: the tile geometry, then the used coefficients.
+template <class A>
+static std::vector<unsigned char> seg_args(const TileProg<A>& P) {
   using C = typename A::C;
   const size_t off = (sizeof(TileGeom) + alignof(C) - 1) / alignof(C) * alignof(C);
   const size_t nc = (size_t)std::max(P.ncoef, 1);
   std::vector<unsigned char> args((off + nc * sizeof(C) + 15) / 16 * 16, 0);
   std::memcpy(args.data(), &P.g, sizeof(TileGeom));
   std::memcpy(args.data() + off, P.coef, (size_t)P.ncoef * sizeof(C));
+  return args;
+}
+
+template <class A>
+int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, const char* prof_name,
+               bool* launched) {
+  *launched = false;
+  if (!jit_enabled_for(sv->n)) return LQS_OK;
+  Entry* e = entry_for(P, r, false, false, nullptr);
+  if (!e || e->state != 1) return LQS_OK;
+  const int dev = sv->device;
+  if (dev < 0 || dev >= kJitMaxDevices) return LQS_OK;
+  const int threads = 1 << (P.g.k - r);
+  const size_t smem = 3 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;  // incoming tile, two exchange buffers
+  CUfunction fn;
+  int per_sm;
+  LQS_TRY(entry_function(e, dev, smem, threads, &fn, &per_sm));
+  std::vector<unsigned char> args = seg_args(P);
   void* psi = sv->d;
   int* status = sv->d_status;
   void* kp[] = {&psi, args.data(), &status};
   const uint64_t grid = std::min<uint64_t>(P.g.ntiles, (uint64_t)std::max(sv->sms, 1) * per_sm);
   ProfScope ps(sv->stream, prof_name, bytes, flops);
-  const CUresult rr = g_drv.launch(fn, (unsigned)grid, 1, 1, kTileThreads, 1, 1, (unsigned)smem,
+  const CUresult rr = g_drv.launch(fn, (unsigned)grid, 1, 1, threads, 1, 1, (unsigned)smem,
                                    (CUstream)sv->stream, kp, nullptr);
   if (rr != CUDA_SUCCESS) return cu_error(rr, "cuLaunchKernel(compiled segment)");
   count_launch();
@@ -994,15 +1322,74 @@ int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, 
   return LQS_OK;
 }
 
-template int jit_source<ArF32>(const TileProg<ArF32>&, int, std::string&, std::string&, std::string&);
-template int jit_source<ArF64>(const TileProg<ArF64>&, int, std::string&, std::string&, std::string&);
-template int jit_source<ArDF>(const TileProg<ArDF>&, int, std::string&, std::string&, std::string&);
+template <class A>
+int jit_adjoint_entry(const TileProg<A>& P, int r, void** entry, std::string* why) {
+  Entry* e = entry_for(P, r, true, true, why);
+  if (!e) return LQS_ERR_UNSUPPORTED;
+  *entry = e;
+  return LQS_OK;
+}
+
+size_t jit_adjoint_smem(int k, int r, size_t amp_bytes) {
+  const int warps = (1 << (k - r)) / 32;
+  return 4 * (amp_bytes << k) + sizeof(double) * warps * kMaxGradSlotsJit + 16;
+}
+
+template <class A>
+int jit_adjoint_occupancy(void* entry, const TileProg<A>& P, int r, SV* sv, int* per_sm) {
+  Entry* e = static_cast<Entry*>(entry);
+  if (e->state != 1) return set_error(LQS_ERR_UNSUPPORTED, "compiled adjoint segment is not available");
+  const int dev = sv->device;
+  if (dev < 0 || dev >= kJitMaxDevices) return set_error(LQS_ERR_UNSUPPORTED, "device index above 63");
+  CUfunction fn;
+  return entry_function(e, dev, jit_adjoint_smem(P.g.k, r, sizeof(typename A::S)), 1 << (P.g.k - r), &fn, per_sm);
+}
+
+template <class A>
+int jit_launch_adjoint(void* entry, const TileProg<A>& P, int r, SV* sv, void* lam, double* partial, unsigned grid,
+                       double bytes, double flops, const char* prof_name) {
+  Entry* e = static_cast<Entry*>(entry);
+  if (e->state != 1) return set_error(LQS_ERR_UNSUPPORTED, "compiled adjoint segment is not available");
+  const int dev = sv->device;
+  if (dev < 0 || dev >= kJitMaxDevices) return set_error(LQS_ERR_UNSUPPORTED, "device index above 63");
+  const int threads = 1 << (P.g.k - r);
+  const size_t smem = jit_adjoint_smem(P.g.k, r, sizeof(typename A::S));
+  CUfunction fn;
+  int per_sm;
+  LQS_TRY(entry_function(e, dev, smem, threads, &fn, &per_sm));
+  std::vector<unsigned char> args = seg_args(P);
+  void* psi = sv->d;
+  int* status = sv->d_status;
+  void* kp[] = {&psi, &lam, args.data(), &partial, &status};
+  ProfScope ps(sv->stream, prof_name, bytes, flops);
+  const CUresult rr = g_drv.launch(fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, (CUstream)sv->stream, kp, nullptr);
+  if (rr != CUDA_SUCCESS) return cu_error(rr, "cuLaunchKernel(compiled adjoint segment)");
+  count_launch();
+  ++g_launches;
+  return LQS_OK;
+}
+
+template int jit_source<ArF32>(const TileProg<ArF32>&, int, std::string&, std::string&, std::string&, bool);
+template int jit_source<ArF64>(const TileProg<ArF64>&, int, std::string&, std::string&, std::string&, bool);
+template int jit_source<ArDF>(const TileProg<ArDF>&, int, std::string&, std::string&, std::string&, bool);
 template int jit_note<ArF32>(const TileProg<ArF32>&, int, int, bool, std::vector<void*>&);
 template int jit_note<ArF64>(const TileProg<ArF64>&, int, int, bool, std::vector<void*>&);
 template int jit_note<ArDF>(const TileProg<ArDF>&, int, int, bool, std::vector<void*>&);
 template int jit_launch<ArF32>(const TileProg<ArF32>&, int, SV*, double, double, const char*, bool*);
 template int jit_launch<ArF64>(const TileProg<ArF64>&, int, SV*, double, double, const char*, bool*);
 template int jit_launch<ArDF>(const TileProg<ArDF>&, int, SV*, double, double, const char*, bool*);
+template int jit_adjoint_entry<ArF32>(const TileProg<ArF32>&, int, void**, std::string*);
+template int jit_adjoint_occupancy<ArF32>(void*, const TileProg<ArF32>&, int, SV*, int*);
+template int jit_adjoint_occupancy<ArF64>(void*, const TileProg<ArF64>&, int, SV*, int*);
+template int jit_adjoint_occupancy<ArDF>(void*, const TileProg<ArDF>&, int, SV*, int*);
+template int jit_adjoint_entry<ArF64>(const TileProg<ArF64>&, int, void**, std::string*);
+template int jit_adjoint_entry<ArDF>(const TileProg<ArDF>&, int, void**, std::string*);
+template int jit_launch_adjoint<ArF32>(void*, const TileProg<ArF32>&, int, SV*, void*, double*, unsigned, double, double,
+                                       const char*);
+template int jit_launch_adjoint<ArF64>(void*, const TileProg<ArF64>&, int, SV*, void*, double*, unsigned, double, double,
+                                       const char*);
+template int jit_launch_adjoint<ArDF>(void*, const TileProg<ArDF>&, int, SV*, void*, double*, unsigned, double, double,
+                                      const char*);
 
 }  // namespace lqs
 

@@ -14,7 +14,8 @@ bool jit_enabled_for(int n);
 // CUDA C++ source of a register-tile program (LQS_ERR_UNSUPPORTED for a
 // program the generator does not take; the interpreter runs those).
 template <class A>
-int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why);
+int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why,
+               bool adjoint = false);
 // Counts one use of the program's structure and queues it for compilation
 // when the mode asks for it (or `force`).
 template <class A>
@@ -29,5 +30,18 @@ int jit_states(const std::vector<void*>& todo, int* ok, std::string* err);
 template <class A>
 int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, const char* prof_name,
                bool* launched);
+
+// Compiled adjoint: the cache entry of a reverse-sweep program (queued for
+// compilation by the caller through jit_compile), its shared-memory size,
+// and its launch over psi and lambda writing per-block partial sums
+// partial[slot * grid + block].
+template <class A>
+int jit_adjoint_entry(const TileProg<A>& P, int r, void** entry, std::string* why);
+size_t jit_adjoint_smem(int k, int r, size_t amp_bytes);
+template <class A>
+int jit_adjoint_occupancy(void* entry, const TileProg<A>& P, int r, SV* sv, int* per_sm);
+template <class A>
+int jit_launch_adjoint(void* entry, const TileProg<A>& P, int r, SV* sv, void* lam, double* partial, unsigned grid,
+                       double bytes, double flops, const char* prof_name);
 
 }  // namespace lqs

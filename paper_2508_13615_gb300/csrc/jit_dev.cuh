@@ -91,8 +91,126 @@ __device__ __forceinline__ void seg_copy(const TileGeom& G, S* buf, const S* psi
   for (uint32_t row = tid; row < nrows; row += blockDim.x)
     bulk_g2s(buf + (size_t)row * per_row, psi + base + (row == tid ? my_roff : row_offset(G, row)), G.row_bytes, bar);
 }
-__device__ __forceinline__ void seg_expect(const TileGeom& G, uint64_t* bar) {
-  mbar_expect_tx(bar, (1u << G.r) * G.row_bytes);
+__device__ __forceinline__ void seg_expect(const TileGeom& G, uint64_t* bar, uint32_t ntiles = 1) {
+  mbar_expect_tx(bar, ntiles * (1u << G.r) * G.row_bytes);
+}
+
+// ---------------------------------------------------------------------------
+// compiled adjoint: gradient partials Im <lambda|G|psi>
+// ---------------------------------------------------------------------------
+template <class A> struct Dfc;
+template <> struct Dfc<ArF32> {
+  static __device__ __forceinline__ DFC get(const float2& w) { return DFC{DF{w.x, 0.f}, DF{w.y, 0.f}}; }
+};
+template <> struct Dfc<ArF64> {
+  static __device__ __forceinline__ DFC get(const double2& w) { return DFC{d2df(w.x), d2df(w.y)}; }
+};
+template <> struct Dfc<ArDF> {
+  static __device__ __forceinline__ DFC get(const DFC& w) { return w; }
+};
+
+// Per-tile partial sums: double-float for complex128 (the products must keep
+// about 2^-46 relative accuracy), float32 for complex64 states.  Either is
+// added in float64 across tiles.
+template <class A> struct GAcc {
+  using T = DAcc;  // running sum (leading part, accumulated errors)
+  using V = DF;    // one term
+  static __device__ __forceinline__ T zero() { return DAcc{0.f, 0.f}; }
+};
+template <> struct GAcc<ArF32> {
+  using T = float;
+  using V = float;
+  static __device__ __forceinline__ T zero() { return 0.f; }
+};
+
+// acc += sign * Im(conj(l) p) = sign * (l.re p.im - l.im p.re)
+__device__ __forceinline__ void gim_t(DAcc& acc, const DFC& l, const DFC& p, bool neg) {
+  df_mac(acc, neg ? df_neg(l.re) : l.re, p.im);
+  df_mac(acc, neg ? l.im : df_neg(l.im), p.re);
+}
+__device__ __forceinline__ void gim_t(float& acc, const float2& l, const float2& p, bool neg) {
+  const float s = neg ? -1.f : 1.f;
+  acc = __fmaf_rn(s * l.x, p.y, acc);
+  acc = __fmaf_rn(-s * l.y, p.x, acc);
+}
+// acc += sign * Re(conj(l) p) = sign * (l.re p.re + l.im p.im)
+__device__ __forceinline__ void gre_t(DAcc& acc, const DFC& l, const DFC& p, bool neg) {
+  df_mac(acc, neg ? df_neg(l.re) : l.re, p.re);
+  df_mac(acc, neg ? df_neg(l.im) : l.im, p.im);
+}
+__device__ __forceinline__ void gre_t(float& acc, const float2& l, const float2& p, bool neg) {
+  const float s = neg ? -1.f : 1.f;
+  acc = __fmaf_rn(s * l.x, p.x, acc);
+  acc = __fmaf_rn(s * l.y, p.y, acc);
+}
+template <class A>
+__device__ __forceinline__ void gim(typename GAcc<A>::T& acc, const typename A::W& l, const typename A::W& p, bool neg) {
+  if constexpr (sizeof(typename GAcc<A>::T) == sizeof(float)) gim_t(acc, l, p, neg);
+  else gim_t(acc, Dfc<A>::get(l), Dfc<A>::get(p), neg);
+}
+template <class A>
+__device__ __forceinline__ void gre(typename GAcc<A>::T& acc, const typename A::W& l, const typename A::W& p, bool neg) {
+  if constexpr (sizeof(typename GAcc<A>::T) == sizeof(float)) gre_t(acc, l, p, neg);
+  else gre_t(acc, Dfc<A>::get(l), Dfc<A>::get(p), neg);
+}
+
+// One term w = Im(conj(l) p), shared by every Z / P1 partial of a merged
+// diagonal run (those partials are signed sums of the same w_j).
+template <class A>
+__device__ __forceinline__ typename GAcc<A>::V wim(const typename A::W& l, const typename A::W& p) {
+  typename GAcc<A>::T a = GAcc<A>::zero();
+  gim<A>(a, l, p, false);
+  if constexpr (sizeof(typename GAcc<A>::T) == sizeof(float)) return a;
+  else return df_norm(a);
+}
+__device__ __forceinline__ void wadd(DAcc& acc, const DF& w, bool neg) { df_acc(acc, neg ? df_neg(w) : w); }
+__device__ __forceinline__ void wadd(float& acc, float w, bool neg) { acc = neg ? acc - w : acc + w; }
+__device__ __forceinline__ DAcc gneg(const DAcc& a, bool neg) { return neg ? DAcc{-a.s, -a.e} : a; }
+__device__ __forceinline__ float gneg(float a, bool neg) { return neg ? -a : a; }
+
+// Warp sum of a partial, added in float64 by lane 0 to the warp's slot.  All
+// 32 lanes must call it.
+__device__ __forceinline__ void gflush(DAcc a, double* slot) {
+  DF v = df_norm(a);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)});
+  if ((threadIdx.x & 31u) == 0) *slot += df2d(v);
+}
+__device__ __forceinline__ void gflush(float a, double* slot) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if ((threadIdx.x & 31u) == 0) *slot += (double)a;
+}
+
+// Walsh butterfly over the warp: lane l ends with sum_i (-1)^popc(i & l) v_i,
+// so lane 0 holds the plain sum and lane 2^m the sum signed by lane bit m.
+// All 32 lanes must call it.
+__device__ __forceinline__ DF wht(DAcc a) {
+  DF v = df_norm(a);
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const DF o{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
+    v = (lane & (uint32_t)off) ? df_sub(o, v) : df_add(v, o);
+  }
+  return v;
+}
+__device__ __forceinline__ float wht(float v) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = (lane & (uint32_t)off) ? o - v : v + o;
+  }
+  return v;
+}
+// slot += (neg ? -w : w) where `cond` holds (one lane per slot).
+__device__ __forceinline__ void gput(const DF& w, bool cond, bool neg, double* slot) {
+  if (cond) *slot += neg ? -df2d(w) : df2d(w);
+}
+__device__ __forceinline__ void gput(float w, bool cond, bool neg, double* slot) {
+  if (cond) *slot += neg ? -(double)w : (double)w;
 }
 
 // Barrier over a group of warps: named barrier `id` (1..15; 0 is the

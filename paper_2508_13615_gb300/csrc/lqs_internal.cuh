@@ -52,6 +52,7 @@ enum KKind : int {
   K_DIAG2 = 7,   // diagonal 4x4 on bits (t0, t1)
   K_LAYOUT = 8,  // register-tile kernel: move amplitudes to a new register/thread bit layout
   K_DPROD = 9,   // register-tile kernel: merged diagonal run, C * prod_q f_q^bit_q on amplitudes whose cond bits are 1
+  K_GRAD = 10,   // compiled adjoint: gradient partial of a merged run's member (no state change)
 };
 
 // Generators for the adjoint method: a parametrised gate U(theta) with
@@ -141,6 +142,16 @@ int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, cons
 // LQS_ERR_UNSUPPORTED when the segment's program does not fit (split it).
 int reg_tile_qubits(int dtype);
 int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith);
+// Compiled adjoint: the reverse sweep's segments as register-tile programs
+// over psi and lambda.  reg_adjoint_available tells whether this state takes
+// it (mode, size); run_adjoint_compiled launches all segments, writing the
+// per-slot partial sums of Im<lambda|G|psi> (slot_op: the op of each slot).
+bool reg_adjoint_available(const SV* sv, int arith);
+int adjoint_tile_qubits(int dtype);  // tile of the compiled reverse sweep
+int run_adjoint_compiled(SV* sv, const std::vector<KOp>& rev, void* lam, int arith, std::vector<int>& slot_op,
+                         double** partial, int* grid);
+// Host only: compile the reverse sweep's kernels (rev = inverse ops, reversed).
+int adjoint_precompile(int n, int dtype, int arith, const std::vector<KOp>& rev, int* compiled);
 // Segment compiler hooks: note_reg_prog builds a segment's register-tile
 // program (LQS_ERR_UNSUPPORTED when it must be split) and notes it;
 // jit_collect walks a segment the way launch_segment routes and splits it.

@@ -550,6 +550,35 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint(typename A::S* __restr
   }
 }
 
+// Sums the per-block partials of every gradient slot in a fixed order (one
+// block per slot), brings them to the host and adds gen_scale * sum to the
+// gradient of each slot's parameter.
+static int adjoint_finish(SV* sv, const std::vector<KOp>& rev, double* partial, int grid,
+                          const std::vector<int>& slot_owner, int n_params, double* grads) {
+  const size_t nslots = slot_owner.size();
+  double* sums = partial + nslots * (size_t)grid;
+  if (nslots) {
+    k_sum_partials<<<(unsigned)nslots, 256, 0, sv->stream>>>(partial, grid, sums);
+    count_launch();
+    LQS_CUDA_TRY(cudaGetLastError());
+  }
+  std::vector<double> h(nslots);
+  if (nslots)
+    LQS_CUDA_TRY(cudaMemcpyAsync(h.data(), sums, sizeof(double) * nslots, cudaMemcpyDeviceToHost, sv->stream));
+  LQS_CUDA_TRY(cudaStreamSynchronize(sv->stream));
+  int status[2] = {0, 0};
+  LQS_CUDA_TRY(cudaMemcpy(status, sv->d_status, sizeof status, cudaMemcpyDeviceToHost));
+  if (status[0]) {
+    cudaMemset(sv->d_status, 0, 64);
+    return set_error(LQS_ERR_TIMEOUT, "a tile load did not complete (bounded wait expired)");
+  }
+  for (size_t s = 0; s < nslots; ++s) {
+    const KOp& o = rev[slot_owner[s]];
+    if (o.param_slot < n_params) grads[o.param_slot] += o.gen_scale * h[s];
+  }
+  return LQS_OK;
+}
+
 template <class A>
 static int adjoint_t(SV* sv, const std::vector<KOp>& ops, int n_params, const lqs_pauli* terms, int n_terms,
                      double* grads, double* energy) {
@@ -575,6 +604,16 @@ static int adjoint_t(SV* sv, const std::vector<KOp>& ops, int n_params, const lq
   std::vector<KOp> rev;
   rev.reserve(ops.size());
   for (size_t i = ops.size(); i-- > 0;) rev.push_back(inverse_op(ops[i]));
+  if (reg_adjoint_available(sv, 0)) {
+    // compiled reverse sweep: register-tile programs over psi and lambda
+    std::vector<int> slot_op;
+    double* partial = nullptr;
+    int grid = 0;
+    const int ar = std::is_same<A, ArF64>::value ? LQS_ARITH_F64 : LQS_ARITH_DF;
+    const int rc = run_adjoint_compiled(sv, rev, lam, ar, slot_op, &partial, &grid);
+    if (rc == LQS_OK) return adjoint_finish(sv, rev, partial, grid, slot_op, n_params, grads);
+    if (rc != LQS_ERR_UNSUPPORTED) return rc;  // nothing was launched when it is unsupported
+  }
   PlanCfg pc;
   pc.k = k;
   pc.b = b;
@@ -616,7 +655,6 @@ static int adjoint_t(SV* sv, const std::vector<KOp>& ops, int n_params, const lq
   void* scratch = nullptr;
   LQS_TRY(sv_scratch(sv, 1, sizeof(double) * (std::max<size_t>(nslots, 1) * (grid + 1)), &scratch));
   double* partial = static_cast<double*>(scratch);
-  double* sums = partial + nslots * grid;
   static thread_local TileProg<A> P;
   size_t off = 0;
   for (auto& s : segs2) {
@@ -642,26 +680,7 @@ static int adjoint_t(SV* sv, const std::vector<KOp>& ops, int n_params, const lq
     LQS_CUDA_TRY(cudaGetLastError());
     off += ng;
   }
-  if (nslots) {
-    k_sum_partials<<<(unsigned)nslots, 256, 0, sv->stream>>>(partial, grid, sums);
-    count_launch();
-    LQS_CUDA_TRY(cudaGetLastError());
-  }
-  std::vector<double> h(nslots);
-  if (nslots)
-    LQS_CUDA_TRY(cudaMemcpyAsync(h.data(), sums, sizeof(double) * nslots, cudaMemcpyDeviceToHost, sv->stream));
-  LQS_CUDA_TRY(cudaStreamSynchronize(sv->stream));
-  int status[2] = {0, 0};
-  LQS_CUDA_TRY(cudaMemcpy(status, sv->d_status, sizeof status, cudaMemcpyDeviceToHost));
-  if (status[0]) {
-    cudaMemset(sv->d_status, 0, 64);
-    return set_error(LQS_ERR_TIMEOUT, "a tile load did not complete (bounded wait expired)");
-  }
-  for (size_t s = 0; s < nslots; ++s) {
-    const KOp& o = rev[slot_owner[s]];
-    if (o.param_slot < n_params) grads[o.param_slot] += o.gen_scale * h[s];
-  }
-  return LQS_OK;
+  return adjoint_finish(sv, rev, partial, grid, slot_owner, n_params, grads);
 }
 
 int run_adjoint(SV* sv, const std::vector<KOp>& ops, int n_params, const lqs_pauli* terms, int n_terms,

@@ -113,6 +113,7 @@ def _load():
         "lqs_jit_info": (i32, [ctypes.POINTER(lqs_jit_stats)]),
         "lqs_jit_precompile": (i32, [i32, i32, i32, ctypes.POINTER(lqs_op), i32, dp, i32,
                                      ctypes.POINTER(lqs_fuse_cfg), ip]),
+        "lqs_jit_precompile_adjoint": (i32, [i32, i32, i32, ctypes.POINTER(lqs_op), i32, dp, i32, ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -426,4 +427,14 @@ def lqs_jit_precompile(n_qubits: int, dtype, ops, params=None, arith: int = LQS_
     _check(_L.lqs_jit_precompile(int(n_qubits), _dtype_code(dtype), int(arith), oa.ptr(), oa.n, _dptr(p),
                                  int(np.asarray(params).size) if params is not None else 0,
                                  ctypes.byref(c) if c is not None else None, ctypes.byref(n)))
+    return n.value
+
+
+def lqs_jit_precompile_adjoint(n_qubits: int, dtype, ops, params=None, arith: int = LQS_ARITH_AUTO) -> int:
+    """Compiles (host only) the reverse-sweep kernels lqs_adjoint_grad would launch; returns how many."""
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    p = _params(params)
+    n = ctypes.c_int()
+    _check(_L.lqs_jit_precompile_adjoint(int(n_qubits), _dtype_code(dtype), int(arith), oa.ptr(), oa.n, _dptr(p),
+                                         int(np.asarray(params).size) if params is not None else 0, ctypes.byref(n)))
     return n.value

@@ -101,3 +101,75 @@ def test_angles_reuse_the_compiled_kernels(jit_on):
         err = max_abs(sv.numpy(), oracle.run_circuit(b, oracle.basis_state(n, 0)))
     assert L.lqs_jit_info()["compiled"] == compiled
     assert err <= TOL["c128"]
+
+
+# ---------------------------------------------------------------------------
+# compiled adjoint (reverse sweep over psi and lambda in registers)
+# ---------------------------------------------------------------------------
+PARAM_GATES = ["RX", "RY", "RZ", "PhaseShift", "Rot", "ControlledPhaseShift", "CRY", "H", "CNOT", "SWAP", "Toffoli",
+               "S", "U4", "Y", "CZ"]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n,layers", [(13, 6), (15, 4)])
+def test_compiled_adjoint_matches_parameter_shift(jit_on, dtype, arith, n, layers):
+    """Ansatz (RY, RZ merged into diagonal runs, CNOT renamings) with the TFIM
+    observable: every gradient against the oracle's parameter shift."""
+    L, before = jit_on
+    set_mode(arith)
+    c = W.ansatz(n, layers, 6)
+    terms = W.tfim(n)
+    g_ref = oracle.param_shift_grad(c, terms)
+    e_ref = oracle.energy(c, terms)
+    with gpu_state(n, dtype) as sv:
+        sv.apply(c, fused=True)
+        g, e = sv.adjoint_grad(c, terms)
+        back = sv.numpy()
+    tol = 1e-10 if dtype == "c128" else 5e-4
+    assert abs(e - e_ref) <= tol
+    np.testing.assert_allclose(g, g_ref, atol=tol)
+    assert abs(back[0] - 1.0) <= (1e-12 if dtype == "c128" else 1e-5)
+    assert L.lqs_jit_info()["launches"] > before["launches"]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_compiled_adjoint_all_parametrised_gates(jit_on, dtype, arith):
+    """Every parametrised gate (RX/RY/RZ, PhaseShift and ControlledPhaseShift
+    with P1 generators, decomposed Rot, CRY) among permutations and dense
+    gates, from a Gaussian state, with controls and targets inside and
+    outside the tile."""
+    set_mode(arith)
+    n = 13
+    c = W.random_circuit(n, 140, seed=17, names=PARAM_GATES)
+    psi0 = W.gaussian_state(n, 18)
+    terms = W.tfim(n) + [W.pauli_word(0.3, {0: "Y", 7: "X", 12: "Z"})]
+    g_ref = oracle.param_shift_grad(c, terms, psi0)
+    with gpu_state(n, dtype, psi0) as sv:
+        sv.apply(c, fused=True)
+        g, _ = sv.adjoint_grad(c, terms)
+    tol = 1e-10 if dtype == "c128" else 5e-4
+    np.testing.assert_allclose(g, g_ref, atol=tol)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_compiled_adjoint_matches_interpreter_sweep(dtype, arith):
+    """Same circuit and state: gradients of the compiled sweep (LQS_JIT_ON)
+    and of the shared-memory sweep (LQS_JIT_OFF)."""
+    import paper_2508_13615_gb300 as L
+    set_mode(arith)
+    n = 18
+    c = W.ansatz(n, 5, 9)
+    terms = W.tfim(n)
+    out = {}
+    old = L.lqs_jit_info()["mode"]
+    try:
+        for mode in (L.LQS_JIT_OFF, L.LQS_JIT_ON):
+            L.lqs_set_jit(mode)
+            with gpu_state(n, dtype) as sv:
+                sv.apply(c, fused=True)
+                out[mode] = sv.adjoint_grad(c, terms)
+    finally:
+        L.lqs_set_jit(old)
+    tol = 1e-10 if dtype == "c128" else 5e-4
+    np.testing.assert_allclose(out[L.LQS_JIT_ON][0], out[L.LQS_JIT_OFF][0], atol=tol)
+    assert abs(out[L.LQS_JIT_ON][1] - out[L.LQS_JIT_OFF][1]) <= tol

@@ -73,11 +73,16 @@ def test_named_barriers_are_never_shared(tmp_path, monkeypatch):
         for seed in (61, 62):
             c = W.random_circuit(n, 160, seed=seed)
             L.lqs_jit_precompile(n, dtype, c.ops, c.params, arith)
+        c = W.random_circuit(n, 80, seed=63)
+        L.lqs_jit_precompile_adjoint(n, dtype, c.ops, c.params, arith)
     files = glob.glob(str(tmp_path / "*.cu"))
     assert files
     groups = 0
+    assert any("lqs_adj_" in f for f in files) and any("lqs_seg_" in f for f in files)
     for f in files:
-        body = open(f).read().split("for (; t < G.ntiles; t += gridDim.x) {", 1)[1]
+        src = open(f).read()
+        nthreads = int(re.search(r"__launch_bounds__\((\d+),", src).group(1))
+        body = src.split("for (; t < G.ntiles; t += gridDim.x) {", 1)[1]
         used = set()
         for line in body.splitlines():
             if "__syncthreads" in line:
@@ -87,6 +92,22 @@ def test_named_barriers_are_never_shared(tmp_path, monkeypatch):
                 groups += 1
                 ids = set(range(int(m.group(1)), int(m.group(1)) + (1 << m.group(2).count("tid >>"))))
                 assert not ids & used and max(ids) <= 15, (f, line)
-                assert int(m.group(3)) * len(ids) == 256, line  # the groups cover the block exactly
+                assert int(m.group(3)) * len(ids) == nthreads, line  # the groups cover the block exactly
                 used |= ids
     assert groups > 0
+
+
+@pytest.mark.parametrize("dtype,arith", ARITHS)
+def test_adjoint_kernels_compile(dtype, arith):
+    """The reverse sweep's kernels (psi and lambda in registers, gradient
+    partials) compile for every parametrised gate, arithmetic and dtype."""
+    before = L.lqs_jit_info()
+    names = ["RX", "RY", "RZ", "PhaseShift", "Rot", "ControlledPhaseShift", "CRY", "H", "CNOT", "SWAP", "Toffoli",
+             "S", "U4", "Y", "CZ"]
+    c = W.random_circuit(13, 100, seed=41, names=names)
+    L.lqs_jit_precompile_adjoint(13, dtype, c.ops, c.params, arith)
+    after = L.lqs_jit_info()
+    assert after["failed"] == before["failed"], after["last_error"]
+    # a state that fits one adjoint tile compiles nothing
+    c = W.ansatz(9, 2, 1)
+    assert L.lqs_jit_precompile_adjoint(9, dtype, c.ops, c.params, arith) == 0
