@@ -300,6 +300,8 @@ def config_adjoint24(args):
         t_jit = time.perf_counter()
         L.lqs_jit_precompile(n, dtype, c.ops, c.params, ar)
         L.lqs_jit_precompile_adjoint(n, dtype, c.ops, c.params, ar)
+        L.lqs_jit_precompile_expval(n, dtype, terms, False, ar)
+        L.lqs_jit_precompile_expval(n, dtype, terms, True, ar)
         jit_s = time.perf_counter() - t_jit
         sv = L.StateVector(n, dtype)
         st = torch.cuda.current_stream()
@@ -520,6 +522,7 @@ def main():
     L.lqs_set_jit(L.LQS_JIT_ON)
     t_jit = time.perf_counter()
     n_jit = sum(L.lqs_jit_precompile(n, "c128", c.ops, c.params, L.LQS_ARITH_DF) for c in (wl.ansatz, wl.qft))
+    n_jit += L.lqs_jit_precompile_expval(n, "c128", wl.tfim, False, L.LQS_ARITH_DF)
     jit_s = time.perf_counter() - t_jit
 
     for _ in range(args.warmup):

@@ -317,6 +317,14 @@ LQS_API int lqs_jit_precompile(int n_qubits, int dtype, int arith, const lqs_op*
  * shared-memory sweep and compile nothing here. */
 LQS_API int lqs_jit_precompile_adjoint(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops,
                                        const double* params, int n_params, int* n_compiled);
+/* The same for the expectation-value passes of lqs_expval on these terms (lambda = 0), or for the passes
+ * that also form lambda = H psi in lqs_adjoint_grad (lambda != 0).  Each pass covers the words whose X/Y
+ * qubits fit one tile (2^11 amplitudes for c128, 2^12 for c64, up to 32 words): thread registers hold the
+ * tile, diagonal words are evaluated together through one Walsh butterfly per warp and register-bit sign
+ * pattern, X/Y words pair amplitudes.  Words wider than a tile, and states of one tile, use the
+ * interpreter passes and compile nothing here. */
+LQS_API int lqs_jit_precompile_expval(int n_qubits, int dtype, int arith, const lqs_pauli* terms, int n_terms,
+                                      int lambda, int* n_compiled);
 
 /* Per-launch profile records (tracing).  Between lqs_profile_start and
  * lqs_profile_stop every kernel the library launches is bracketed by CUDA

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "arith.cuh"
@@ -426,6 +427,24 @@ int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* param
   }
   for (const Segment& s : segs) LQS_TRY(launch_segment(sv, kops, s, pc, arith));
   return LQS_OK;
+}
+
+int lqs_jit_precompile_expval(int n_qubits, int dtype, int arith, const lqs_pauli* terms, int n_terms, int lambda,
+                              int* n_compiled) {
+  if (n_compiled) *n_compiled = 0;
+  if (n_qubits < 1 || n_qubits > 36) return set_error(LQS_ERR_ARG, "n_qubits must be in [1, 36]");
+  if (dtype != LQS_C64 && dtype != LQS_C128) return set_error(LQS_ERR_ARG, "bad dtype");
+  if (arith != LQS_ARITH_AUTO && arith != LQS_ARITH_F64 && arith != LQS_ARITH_DF)
+    return set_error(LQS_ERR_ARG, "arith must be LQS_ARITH_AUTO, LQS_ARITH_F64 or LQS_ARITH_DF");
+  if (n_terms < 0 || (n_terms > 0 && !terms)) return set_error(LQS_ERR_ARG, "bad terms");
+  const uint64_t all = n_qubits >= 64 ? ~0ull : ((1ull << n_qubits) - 1);
+  for (int i = 0; i < n_terms; ++i)
+    if ((terms[i].x_mask | terms[i].z_mask) & ~all) return set_error(LQS_ERR_ARG, "a term acts on a qubit >= n");
+  if (n_terms == 0 || n_qubits <= (dtype == LQS_C64 ? 12 : 11)) return LQS_OK;  // nothing compiled for these
+  const int rc = pauli_precompile(n_qubits, dtype, current_arith(arith), terms, n_terms, lambda != 0, n_compiled);
+  if (rc == LQS_ERR_UNSUPPORTED && std::string(lqs_last_error()).find("do not fit") != std::string::npos)
+    return LQS_OK;  // words wider than a tile run on the interpreter passes
+  return rc;
 }
 
 int lqs_jit_precompile_adjoint(int n_qubits, int dtype, int arith, const lqs_op* ops, int n_ops,

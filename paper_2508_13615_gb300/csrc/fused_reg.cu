@@ -814,7 +814,7 @@ static int adj_build(int n, const std::vector<KOp>& rev, const Segment& seg, int
 // call compiled.
 template <class A>
 static int adj_prepare_t(int n, int dtype, const std::vector<KOp>& rev, std::vector<std::unique_ptr<AdjProg<A>>>& progs,
-                         int* compiled) {
+                         int* compiled, bool force) {
   int r, tb;
   adj_shape(dtype, &r, &tb);
   const int k = r + tb, b = dtype == LQS_C64 ? 5 : 4;
@@ -831,6 +831,8 @@ static int adj_prepare_t(int n, int dtype, const std::vector<KOp>& rev, std::vec
     std::string why;
     if (jit_adjoint_entry(pr->P, r, &pr->entry, &why) != LQS_OK)
       return set_error(LQS_ERR_UNSUPPORTED, "adjoint segment not compiled: " + why);
+    if (!force && !jit_should_compile(pr->entry, n))
+      return set_error(LQS_ERR_UNSUPPORTED, "adjoint segment not compiled yet");
     if (std::find(todo.begin(), todo.end(), pr->entry) == todo.end()) todo.push_back(pr->entry);
   }
   int before = 0;
@@ -850,7 +852,7 @@ static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam
   adj_shape(sv->dtype, &r, &tb);
   const int n = sv->n, k = r + tb;
   std::vector<std::unique_ptr<AdjProg<A>>> progs;
-  LQS_TRY(adj_prepare_t<A>(n, sv->dtype, rev, progs, nullptr));
+  LQS_TRY(adj_prepare_t<A>(n, sv->dtype, rev, progs, nullptr, false));
   size_t nslots = 0;
   for (auto& pr : progs) nslots += pr->gops.size();
   // one grid for all segments (the partial sums share a layout): as many
@@ -885,14 +887,14 @@ static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam
 int adjoint_precompile(int n, int dtype, int arith, const std::vector<KOp>& rev, int* compiled) {
   if (dtype == LQS_C64) {
     std::vector<std::unique_ptr<AdjProg<ArF32>>> p;
-    return adj_prepare_t<ArF32>(n, dtype, rev, p, compiled);
+    return adj_prepare_t<ArF32>(n, dtype, rev, p, compiled, true);
   }
   if (arith == LQS_ARITH_F64) {
     std::vector<std::unique_ptr<AdjProg<ArF64>>> p;
-    return adj_prepare_t<ArF64>(n, dtype, rev, p, compiled);
+    return adj_prepare_t<ArF64>(n, dtype, rev, p, compiled, true);
   }
   std::vector<std::unique_ptr<AdjProg<ArDF>>> p;
-  return adj_prepare_t<ArDF>(n, dtype, rev, p, compiled);
+  return adj_prepare_t<ArDF>(n, dtype, rev, p, compiled, true);
 }
 
 int run_adjoint_compiled(SV* sv, const std::vector<KOp>& rev, void* lam, int arith, std::vector<int>& slot_op,

@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <nvrtc.h>
 
+#include <functional>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -1364,6 +1366,56 @@ int jit_launch_adjoint(void* entry, const TileProg<A>& P, int r, SV* sv, void* l
   ProfScope ps(sv->stream, prof_name, bytes, flops);
   const CUresult rr = g_drv.launch(fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, (CUstream)sv->stream, kp, nullptr);
   if (rr != CUDA_SUCCESS) return cu_error(rr, "cuLaunchKernel(compiled adjoint segment)");
+  count_launch();
+  ++g_launches;
+  return LQS_OK;
+}
+
+void* jit_entry_generic(const std::string& key,
+                        const std::function<bool(std::string& src, std::string& name, std::string& why)>& gen,
+                        bool count_use, std::string* why) {
+  if (Entry* e = find_key(key, count_use)) return e;
+  std::string src, name, w;
+  if (!gen(src, name, w)) {
+    if (why) *why = w;
+    return nullptr;
+  }
+  Entry* e = find_or_add(src, name, count_use);
+  if (!e) {
+    if (why) *why = "compiled-kernel cache is full";
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_keys.emplace(key, e);
+  return e;
+}
+
+bool jit_should_compile(void* entry, int n) {
+  Entry* e = static_cast<Entry*>(entry);
+  std::lock_guard<std::mutex> lk(g_mu);
+  return e->state == 1 || (e->state == 0 && wants_compile(*e, n));
+}
+
+int jit_occupancy_generic(void* entry, int dev, size_t smem, int threads, int* per_sm) {
+  Entry* e = static_cast<Entry*>(entry);
+  if (e->state != 1) return set_error(LQS_ERR_UNSUPPORTED, "compiled kernel is not available");
+  if (dev < 0 || dev >= kJitMaxDevices) return set_error(LQS_ERR_UNSUPPORTED, "device index above 63");
+  CUfunction fn;
+  return entry_function(e, dev, smem, threads, &fn, per_sm);
+}
+
+int jit_launch_generic(void* entry, SV* sv, unsigned grid, int threads, size_t smem, void** params,
+                       const char* prof_name, double bytes, double flops) {
+  Entry* e = static_cast<Entry*>(entry);
+  if (e->state != 1) return set_error(LQS_ERR_UNSUPPORTED, "compiled kernel is not available");
+  const int dev = sv->device;
+  if (dev < 0 || dev >= kJitMaxDevices) return set_error(LQS_ERR_UNSUPPORTED, "device index above 63");
+  CUfunction fn;
+  int per_sm;
+  LQS_TRY(entry_function(e, dev, smem, threads, &fn, &per_sm));
+  ProfScope ps(sv->stream, prof_name, bytes, flops);
+  const CUresult rr = g_drv.launch(fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, (CUstream)sv->stream, params, nullptr);
+  if (rr != CUDA_SUCCESS) return cu_error(rr, "cuLaunchKernel(compiled kernel)");
   count_launch();
   ++g_launches;
   return LQS_OK;

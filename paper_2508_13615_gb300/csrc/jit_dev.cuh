@@ -213,6 +213,72 @@ __device__ __forceinline__ void gput(float w, bool cond, bool neg, double* slot)
   if (cond) *slot += neg ? -(double)w : (double)w;
 }
 
+// ---------------------------------------------------------------------------
+// compiled Pauli passes: |psi_j|^2, lambda accumulators
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ DF pnorm2(const DFC& v) {
+  DAcc a = df_prod(v.re, v.re);
+  df_mac(a, v.im, v.im);
+  return df_norm(a);
+}
+__device__ __forceinline__ float pnorm2(const float2& v) { return __fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)); }
+template <class A>
+__device__ __forceinline__ typename GAcc<A>::V pn2(const typename A::W& w) {
+  if constexpr (sizeof(typename GAcc<A>::T) == sizeof(float)) return pnorm2(w);
+  else return pnorm2(Dfc<A>::get(w));
+}
+
+// lambda_j accumulated per component: double-float for complex128 states,
+// float32 for complex64.
+template <class A> struct LAcc {
+  DAcc re, im;
+  __device__ __forceinline__ void init(const typename A::W& w) {
+    const DFC v = Dfc<A>::get(w);
+    re = DAcc{v.re.h, v.re.l};
+    im = DAcc{v.im.h, v.im.l};
+  }
+  __device__ __forceinline__ void zero() { re = im = DAcc{0.f, 0.f}; }
+  // += c * sign * i^PH * w
+  template <int PH>
+  __device__ __forceinline__ void add(const typename A::W& w, const DF& c, bool neg) {
+    const DFC v = Dfc<A>::get(w);
+    DF vr = v.re, vi = v.im;
+    if (PH & 1) { const DF t = vr; vr = df_neg(vi); vi = t; }
+    if (PH & 2) { vr = df_neg(vr); vi = df_neg(vi); }
+    if (neg) { vr = df_neg(vr); vi = df_neg(vi); }
+    df_mac(re, vr, c);
+    df_mac(im, vi, c);
+  }
+  __device__ __forceinline__ typename A::W out() const;
+};
+template <> __device__ __forceinline__ DFC LAcc<ArDF>::out() const { return DFC{df_norm(re), df_norm(im)}; }
+template <> __device__ __forceinline__ double2 LAcc<ArF64>::out() const {
+  return make_double2(df2d(df_norm(re)), df2d(df_norm(im)));
+}
+template <> struct LAcc<ArF32> {
+  float re, im;
+  __device__ __forceinline__ void init(const float2& w) { re = w.x; im = w.y; }
+  __device__ __forceinline__ void zero() { re = im = 0.f; }
+  template <int PH>
+  __device__ __forceinline__ void add(const float2& w, float c, bool neg) {
+    float vr = w.x, vi = w.y;
+    if (PH & 1) { const float t = vr; vr = -vi; vi = t; }
+    if (PH & 2) { vr = -vr; vi = -vi; }
+    if (neg) { vr = -vr; vi = -vi; }
+    re = __fmaf_rn(vr, c, re);
+    im = __fmaf_rn(vi, c, im);
+  }
+  __device__ __forceinline__ float2 out() const { return make_float2(re, im); }
+};
+// Real coefficient of a Pauli word in the parameter block, per policy.
+template <class A> struct PCoef { using T = DF; };
+template <> struct PCoef<ArF32> { using T = float; };
+// sum of signed coefficients (diagonal words of lambda)
+__device__ __forceinline__ void cadd(DAcc& a, const DF& c, bool neg) { df_acc(a, neg ? df_neg(c) : c); }
+__device__ __forceinline__ void cadd(float& a, float c, bool neg) { a = neg ? a - c : a + c; }
+__device__ __forceinline__ DF cfin(const DAcc& a) { return df_norm(a); }
+__device__ __forceinline__ float cfin(float a) { return a; }
+
 // Barrier over a group of warps: named barrier `id` (1..15; 0 is the
 // block-wide barrier) for `nthreads` threads, a multiple of 32.
 __device__ __forceinline__ void bar_group(uint32_t id, uint32_t nthreads) {

@@ -164,6 +164,13 @@ int jit_collect(int n, int dtype, int arith, const std::vector<KOp>& ops, const 
 // reductions / expectation values / adjoint
 // ---------------------------------------------------------------------------
 int run_norm2(SV* sv, int arith, double* out);
+// Fixed-order sums of per-block partials: sums[s] = sum_b partial[s * grid + b].
+int k_sum_partials_launch(double* partial, int grid, double* sums, int slots, cudaStream_t st);
+// Compiled Pauli passes (<P_w> per word into vals; lambda = H psi when lam is
+// non-null).  LQS_ERR_UNSUPPORTED when this state or word set does not take
+// them (the interpreter passes run instead); nothing is launched then.
+int pauli_compiled(SV* sv, const lqs_pauli* terms, int n_terms, void* lam, int arith, double* vals);
+int pauli_precompile(int n, int dtype, int arith, const lqs_pauli* terms, int n_terms, bool lambda, int* compiled);
 int run_expval(SV* sv, const lqs_pauli* terms, int n_terms, const PlanCfg& pc, int arith, double* out,
                double* per_term, const void* lambda_out);
 int run_adjoint(SV* sv, const std::vector<KOp>& ops, int n_params, const lqs_pauli* terms, int n_terms,

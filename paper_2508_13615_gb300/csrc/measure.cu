@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "jit.h"
 #include "lqs_internal.cuh"
 #include "tile.cuh"
 #include "tile_ops.cuh"
@@ -282,6 +283,14 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
   if (threadIdx.x == 0) out[i] = sh[0];
 }
 
+int k_sum_partials_launch(double* partial, int grid, double* sums, int slots, cudaStream_t st) {
+  if (slots <= 0) return LQS_OK;
+  k_sum_partials<<<(unsigned)slots, 256, 0, st>>>(partial, grid, sums);
+  count_launch();
+  LQS_CUDA_TRY(cudaGetLastError());
+  return LQS_OK;
+}
+
 // Tile size for measurement passes: smaller than the fused default so that
 // two tiles (psi and lambda) plus accumulators leave room for 2-3 CTAs per SM.
 static void measure_kb(int n, int dtype, int& k, int& b) {
@@ -331,6 +340,11 @@ template <class A>
 static int pauli_passes(SV* sv, const lqs_pauli* terms, int n_terms, void* lam, double* vals) {
   int k, b;
   measure_kb(sv->n, sv->dtype, k, b);
+  if (n_terms > 0 && sv->n > k && jit_enabled_for(sv->n)) {  // compiled passes when this state takes them
+    const int ar = std::is_same<A, ArF64>::value ? LQS_ARITH_F64 : LQS_ARITH_DF;
+    const int rc = pauli_compiled(sv, terms, n_terms, lam, ar, vals);
+    if (rc != LQS_ERR_UNSUPPORTED) return rc;
+  }
   std::vector<PassPlan> passes;
   std::vector<int> wide;
   LQS_TRY(plan_passes(sv->n, terms, n_terms, k, b, passes, wide));

@@ -92,7 +92,7 @@ struct PassPlan {
   std::vector<int> words;
 };
 inline int plan_passes(int n, const lqs_pauli* terms, int n_terms, int k, int b, std::vector<PassPlan>& out,
-                       std::vector<int>& wide) {
+                       std::vector<int>& wide, int max_words = kPassWords) {
   std::vector<char> done(n_terms, 0);
   int left = n_terms;
   const uint64_t low = (b >= 64) ? ~0ull : ((1ull << b) - 1);
@@ -105,7 +105,7 @@ inline int plan_passes(int n, const lqs_pauli* terms, int n_terms, int k, int b,
   while (left) {
     PassPlan p;
     p.Q = low;
-    for (int i = 0; i < n_terms && (int)p.words.size() < kPassWords; ++i) {
+    for (int i = 0; i < n_terms && (int)p.words.size() < max_words; ++i) {
       if (done[i]) continue;
       const uint64_t need = terms[i].x_mask & ~p.Q;
       if (__builtin_popcountll(p.Q | need) <= k) {

@@ -114,6 +114,7 @@ def _load():
         "lqs_jit_precompile": (i32, [i32, i32, i32, ctypes.POINTER(lqs_op), i32, dp, i32,
                                      ctypes.POINTER(lqs_fuse_cfg), ip]),
         "lqs_jit_precompile_adjoint": (i32, [i32, i32, i32, ctypes.POINTER(lqs_op), i32, dp, i32, ip]),
+        "lqs_jit_precompile_expval": (i32, [i32, i32, i32, ctypes.POINTER(lqs_pauli), i32, i32, ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -437,4 +438,14 @@ def lqs_jit_precompile_adjoint(n_qubits: int, dtype, ops, params=None, arith: in
     n = ctypes.c_int()
     _check(_L.lqs_jit_precompile_adjoint(int(n_qubits), _dtype_code(dtype), int(arith), oa.ptr(), oa.n, _dptr(p),
                                          int(np.asarray(params).size) if params is not None else 0, ctypes.byref(n)))
+    return n.value
+
+
+def lqs_jit_precompile_expval(n_qubits: int, dtype, terms, lambda_: bool = False, arith: int = LQS_ARITH_AUTO) -> int:
+    """Compiles (host only) the Pauli-pass kernels of lqs_expval (or, with lambda_, of the adjoint's
+    lambda = H psi); returns how many."""
+    pa = terms if isinstance(terms, PauliArray) else PauliArray(terms)
+    n = ctypes.c_int()
+    _check(_L.lqs_jit_precompile_expval(int(n_qubits), _dtype_code(dtype), int(arith), pa.ptr(), pa.n,
+                                        1 if lambda_ else 0, ctypes.byref(n)))
     return n.value

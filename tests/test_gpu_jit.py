@@ -173,3 +173,75 @@ def test_compiled_adjoint_matches_interpreter_sweep(dtype, arith):
     tol = 1e-10 if dtype == "c128" else 5e-4
     np.testing.assert_allclose(out[L.LQS_JIT_ON][0], out[L.LQS_JIT_OFF][0], atol=tol)
     assert abs(out[L.LQS_JIT_ON][1] - out[L.LQS_JIT_OFF][1]) <= tol
+
+
+# ---------------------------------------------------------------------------
+# compiled Pauli passes (expectation values and lambda = H psi)
+# ---------------------------------------------------------------------------
+def random_words(n, count, seed):
+    """Seeded Pauli words of 1..4 factors on any qubits (X, Y and Z land on
+    register, thread and outside-tile bits), real coefficients."""
+    r = W.splitmix64(seed, 0, 6 * count)
+    out = []
+    for i in range(count):
+        m = 1 + int(r[6 * i] % np.uint64(4))
+        word = {}
+        for j in range(m):
+            q = int(r[6 * i + 1 + j] % np.uint64(n))
+            word[q] = "XYZ"[int((r[6 * i + 5] >> np.uint64(2 * j)) % np.uint64(3))]
+        out.append(W.pauli_word(float(W.uniforms(seed + 1, i, 1)[0]) - 0.5, word))
+    return out
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n", [14, 17])
+def test_compiled_expval_random_words(jit_on, dtype, arith, n):
+    L, before = jit_on
+    set_mode(arith)
+    psi0 = W.gaussian_state(n, 300 + n)
+    # words whose X/Y qubits fit a tile (the compiled passes take those)
+    terms = [t for t in random_words(n, 60, 31 + n) if bin(int(t.x_mask)).count("1") <= 3] + W.tfim(n)
+    e_ref, per_ref = oracle.expval(psi0, terms)
+    with gpu_state(n, dtype, psi0) as sv:
+        e, per = sv.expval(terms)
+    tol = 1e-11 if dtype == "c128" else 2e-5
+    np.testing.assert_allclose(per, per_ref, atol=tol)
+    assert abs(e - e_ref) <= tol * sum(abs(t.coeff) for t in terms)
+    assert L.lqs_jit_info()["launches"] > before["launches"]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_compiled_expval_matches_interpreter(dtype, arith):
+    import paper_2508_13615_gb300 as L
+    set_mode(arith)
+    n = 20
+    terms = W.tfim(n) + random_words(n, 20, 77)
+    out = {}
+    old = L.lqs_jit_info()["mode"]
+    try:
+        for mode in (L.LQS_JIT_OFF, L.LQS_JIT_ON):
+            L.lqs_set_jit(mode)
+            with gpu_state(n, dtype) as sv:
+                sv.apply(W.ansatz(n, 3, 12), fused=True)
+                out[mode] = sv.expval(terms)
+    finally:
+        L.lqs_set_jit(old)
+    tol = 1e-11 if dtype == "c128" else 2e-5
+    np.testing.assert_allclose(out[L.LQS_JIT_ON][1], out[L.LQS_JIT_OFF][1], atol=tol)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_compiled_lambda_through_adjoint(jit_on, dtype, arith):
+    """lambda = H psi from the compiled passes, checked through gradients of
+    an observable with X, Y and Z words on register, thread and outside bits."""
+    set_mode(arith)
+    n = 14
+    c = W.ansatz(n, 3, 21)
+    terms = random_words(n, 25, 91) + W.tfim(n)
+    terms = [t for t in terms if bin(int(t.x_mask)).count("1") <= 3]
+    g_ref = oracle.param_shift_grad(c, terms)
+    with gpu_state(n, dtype) as sv:
+        sv.apply(c, fused=True)
+        g, e = sv.adjoint_grad(c, terms)
+    tol = 1e-10 if dtype == "c128" else 5e-4
+    np.testing.assert_allclose(g, g_ref, atol=tol)
