@@ -95,8 +95,10 @@ class SegGen {
   std::ostringstream o_;    // tile-loop body
   std::ostringstream pre_;  // before the tile loop (tile-independent per-thread values)
   std::string why_;
+  std::vector<std::pair<std::string, int>> pend_;  // gradient partials awaiting a batched warp sum
 
   int nthreads() const { return 1 << (k_ - r_); }
+  void flush_pending(bool all);
   // runs f once per state, with V() naming that state's variables
   template <class F>
   void each(F f) {
@@ -325,13 +327,34 @@ void SegGen::emit_store() {
 // its target: X, Y (pairs on the target's register slot), Z (a sign per
 // amplitude), or the projector P1 on its control set.  The per-thread sum is
 // reduced over the warp into the warp's float64 slot.
+// Batched warp sums of pending partials, four at a time (the rest with
+// unused slots when `all`).
+void SegGen::flush_pending(bool all) {
+  while (pend_.size() >= 4 || (all && !pend_.empty())) {
+    std::string a[4], sl[4];
+    for (int i = 0; i < 4; ++i) {
+      if (i < (int)pend_.size()) {
+        a[i] = pend_[i].first;
+        sl[i] = "wacc + warp * " + std::to_string(kMaxGradSlotsJit) + " + " + std::to_string(pend_[i].second);
+      } else {
+        a[i] = "lqs::jit::GAcc<A>::zero()";
+        sl[i] = "(double*)0";
+      }
+    }
+    o_ << "    lqs::jit::gflush4(" << a[0] << ", " << a[1] << ", " << a[2] << ", " << a[3] << ", " << sl[0] << ", "
+       << sl[1] << ", " << sl[2] << ", " << sl[3] << ");\n";
+    pend_.erase(pend_.begin(), pend_.begin() + std::min<size_t>(4, pend_.size()));
+  }
+}
+
 bool SegGen::emit_grad(const TOp& t) {
   if (t.gslot < 0) return true;
   uint32_t regc = 0;
   const std::string p = pred(t.lcmask, t.ecmask, regc);
   auto qual = [&](int e) { return ((uint32_t)e & regc) == regc; };
   const std::string acc = fresh("g");
-  o_ << "    // gradient slot " << t.gslot << "\n    { lqs::jit::GAcc<A>::T " << acc << " = lqs::jit::GAcc<A>::zero();\n";
+  // the accumulator lives at tile scope until its batched warp sum
+  o_ << "    // gradient slot " << t.gslot << "\n    lqs::jit::GAcc<A>::T " << acc << " = lqs::jit::GAcc<A>::zero();\n    {\n";
   if (!p.empty()) o_ << "      if (" << p << ") {\n";
   if (t.gen == G_P1 || (t.gen == G_Z && !(t.l0 >= 0 && reg_slot(t.l0) >= 0))) {
     // single amplitudes; for Z the sign comes from a thread bit or the tile
@@ -362,7 +385,9 @@ bool SegGen::emit_grad(const TOp& t) {
     }
   }
   if (!p.empty()) o_ << "      }\n";
-  o_ << "      lqs::jit::gflush(" << acc << ", wacc + warp * " << kMaxGradSlotsJit << " + " << t.gslot << ");\n    }\n";
+  o_ << "    }\n";
+  pend_.emplace_back(acc, t.gslot);
+  flush_pending(false);
   return true;
 }
 
@@ -852,6 +877,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
       return false;
     }
   }
+  flush_pending(true);
   emit_store();  // natural order, or a layout that keeps sectors on lanes
   const std::string body = o_.str();
   const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^

@@ -183,6 +183,48 @@ __device__ __forceinline__ void gflush(float a, double* slot) {
   if ((threadIdx.x & 31u) == 0) *slot += (double)a;
 }
 
+// Four per-lane partials summed over the warp at once (a reduce-scatter):
+// two halving exchanges leave each lane with one of the four (lanes with bit
+// 4 take slots 2-3, with bit 3 the odd one), three butterfly steps complete
+// the sums, and lanes 0, 8, 16, 24 add them to slots s0..s3 (null: unused).
+// All 32 lanes must call it.
+__device__ __forceinline__ DF shfl_df(const DF& v, int off) {
+  return DF{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
+}
+__device__ __forceinline__ void gflush4(const DAcc& a0, const DAcc& a1, const DAcc& a2, const DAcc& a3, double* s0,
+                                        double* s1, double* s2, double* s3) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const bool u16 = lane & 16u, u8 = lane & 8u;
+  const DF v0 = df_norm(a0), v1 = df_norm(a1), v2 = df_norm(a2), v3 = df_norm(a3);
+  DF k0 = u16 ? v2 : v0, k1 = u16 ? v3 : v1;
+  const DF t0 = u16 ? v0 : v2, t1 = u16 ? v1 : v3;
+  k0 = df_add(k0, shfl_df(t0, 16));
+  k1 = df_add(k1, shfl_df(t1, 16));
+  DF k = u8 ? k1 : k0;
+  k = df_add(k, shfl_df(u8 ? k0 : k1, 8));
+  k = df_add(k, shfl_df(k, 4));
+  k = df_add(k, shfl_df(k, 2));
+  k = df_add(k, shfl_df(k, 1));
+  double* s = u16 ? (u8 ? s3 : s2) : (u8 ? s1 : s0);
+  if ((lane & 7u) == 0 && s) *s += df2d(k);
+}
+__device__ __forceinline__ void gflush4(float a0, float a1, float a2, float a3, double* s0, double* s1, double* s2,
+                                        double* s3) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const bool u16 = lane & 16u, u8 = lane & 8u;
+  float k0 = u16 ? a2 : a0, k1 = u16 ? a3 : a1;
+  const float t0 = u16 ? a0 : a2, t1 = u16 ? a1 : a3;
+  k0 += __shfl_xor_sync(0xffffffffu, t0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, t1, 16);
+  float k = u8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, u8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  double* s = u16 ? (u8 ? s3 : s2) : (u8 ? s1 : s0);
+  if ((lane & 7u) == 0 && s) *s += (double)k;
+}
+
 // Walsh butterfly over the warp: lane l ends with sum_i (-1)^popc(i & l) v_i,
 // so lane 0 holds the plain sum and lane 2^m the sum signed by lane bit m.
 // All 32 lanes must call it.
