@@ -175,6 +175,14 @@ ALU_PEAK_TFLOPS = {"df": FP32_INSTR_PEAK / DF_INSTR_PER_FLOP / 1e12, "f32": 2 * 
                    "f64": 1.25}
 
 
+# DRAM traffic per launch of the dominant kernel family, from the ncu capture
+# summarised in profiles/compiled_segment_ansatz_24q_c128.md (24 qubits,
+# scaled by the 64x units of a 30-qubit launch).  Retake it when the kernels
+# change.
+TRAFFIC = {"k_fused_reg_jit/df": {"bytes_per_launch": (268.6e6 + 211.6e6) * 64,
+                                  "source": "profiles/compiled_segment_ansatz_24q_c128.md (24 q capture x 64)"}}
+
+
 def roofline(records, pk, traffic=None):
     """Dominant kernel family (by device time) and its achieved fraction of the
     binding roof: HBM bandwidth or the arithmetic rate of its precision."""
@@ -205,6 +213,9 @@ def roofline(records, pk, traffic=None):
                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in pk else
                               "fallback 6.8 TB/s",
                "alu_frac": alu_frac}
+    if traffic is None and name in TRAFFIC:
+        traffic = TRAFFIC[name]["bytes_per_launch"]
+        out["traffic_source"] = TRAFFIC[name]["source"]
     out.update({"traffic": traffic, "launches": cnt, "share": ms / total, "bytes_per_launch": b / cnt,
                 "ms_per_launch": ms / cnt, "f64eq_tflops": tfl, "algorithmic_gbps": gbs})
     fams = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total, 4),
