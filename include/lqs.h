@@ -175,6 +175,17 @@ LQS_API int lqs_apply_matrix(lqs_sv* sv, const int* wires, int n_wires, const do
 LQS_API int lqs_apply_fused(lqs_sv* sv, const lqs_op* ops, int n_ops, const double* params, int n_params,
                     const lqs_fuse_cfg* cfg_or_null);
 
+/* Autotuner (the tuner of the batched driver, Sec. 4 / Listing 1's repeated circuits): times
+ * lqs_apply_fused on this state with candidate configurations (low contiguous tile qubits b = 3..5
+ * for c128, 4..6 for c64; no segment cap or 48 gates), each applied twice untimed (compiled kernels
+ * are built then) and `repeats` (1..100) times under CUDA events on the state's stream.  *best
+ * receives the fastest, which is also remembered for this qubit count, dtype and circuit structure
+ * (gates and wires; not angles or matrices): later lqs_apply_fused calls with cfg_or_null = NULL on
+ * that structure use it.  The state serves as scratch: its contents are undefined on return.  States
+ * of one tile have nothing to tune (*best = all zero).  Synchronous. */
+LQS_API int lqs_autotune_fused(lqs_sv* sv, const lqs_op* ops, int n_ops, const double* params, int n_params,
+                               int repeats, lqs_fuse_cfg* best);
+
 /* Host-only view of the fused plan (no GPU work, usable without a device):
  * *n_segments receives the number of HBM passes; when seg_qubit_mask is
  * non-null it receives each segment's tile qubit set (capacity `cap`), and

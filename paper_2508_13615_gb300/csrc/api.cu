@@ -414,6 +414,8 @@ int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* param
   SV* sv = S_(h);
   std::vector<KOp> kops;
   LQS_TRY(lower_ops(sv->n, ops, n_ops, params, n_params, false, kops));
+  lqs_fuse_cfg tuned;
+  if (!cfg && tuned_cfg(sv->n, sv->dtype, ops, n_ops, &tuned)) cfg = &tuned;  // lqs_autotune_fused's choice
   PlanCfg pc;
   int arith = LQS_ARITH_AUTO;
   LQS_TRY(resolve_cfg(sv->n, sv->dtype, cfg, pc, &arith));

@@ -136,6 +136,8 @@ struct PlanCfg {
   int max_ops = 0; // per-segment cap
 };
 int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* arith);
+// The configuration lqs_autotune_fused chose for this circuit structure, if any.
+bool tuned_cfg(int n, int dtype, const lqs_op* ops, int n_ops, lqs_fuse_cfg* out);
 int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::vector<Segment>& segs);
 int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith);
 // Register-resident tile kernel (k = reg_tile_qubits(dtype)); returns

@@ -115,6 +115,7 @@ def _load():
                                      ctypes.POINTER(lqs_fuse_cfg), ip]),
         "lqs_jit_precompile_adjoint": (i32, [i32, i32, i32, ctypes.POINTER(lqs_op), i32, dp, i32, ip]),
         "lqs_jit_precompile_expval": (i32, [i32, i32, i32, ctypes.POINTER(lqs_pauli), i32, i32, ip]),
+        "lqs_autotune_fused": (i32, [vp, ctypes.POINTER(lqs_op), i32, dp, i32, i32, ctypes.POINTER(lqs_fuse_cfg)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -449,3 +450,15 @@ def lqs_jit_precompile_expval(n_qubits: int, dtype, terms, lambda_: bool = False
     _check(_L.lqs_jit_precompile_expval(int(n_qubits), _dtype_code(dtype), int(arith), pa.ptr(), pa.n,
                                         1 if lambda_ else 0, ctypes.byref(n)))
     return n.value
+
+
+def lqs_autotune_fused(h, ops, params, repeats: int = 2) -> dict:
+    """Times fused-path configurations on this state (used as scratch); returns the fastest, which later
+    lqs_apply_fused calls without a cfg use for this circuit structure."""
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    p = _params(params)
+    best = lqs_fuse_cfg()
+    _check(_L.lqs_autotune_fused(h, oa.ptr(), oa.n, _dptr(p), int(np.asarray(params).size) if params is not None else 0,
+                                 int(repeats), ctypes.byref(best)))
+    return {"tile_qubits": best.tile_qubits, "low_qubits": best.low_qubits, "arith": best.arith,
+            "max_ops": best.max_ops}

@@ -245,3 +245,21 @@ def test_compiled_lambda_through_adjoint(jit_on, dtype, arith):
         g, e = sv.adjoint_grad(c, terms)
     tol = 1e-10 if dtype == "c128" else 5e-4
     np.testing.assert_allclose(g, g_ref, atol=tol)
+
+
+def test_autotune_choice_is_used_and_correct(jit_on):
+    """The tuner returns one of its candidates; lqs_apply_fused without a
+    configuration then uses it, and the result matches the oracle."""
+    L, _ = jit_on
+    set_mode("df")
+    n = 17
+    c = W.ansatz(n, 3, 41)
+    with gpu_state(n, "c128") as sv:
+        best = L.lqs_autotune_fused(sv.h, c.ops, c.params, 1)
+        assert best["low_qubits"] in (3, 4, 5) and best["max_ops"] in (0, 48)
+        sv.set_basis(0)
+        sv.apply(c, fused=True)  # no cfg: the tuned one
+        err = max_abs(sv.numpy(), oracle.run_circuit(c, oracle.basis_state(n, 0)))
+    assert err <= TOL["c128"]
+    n_seg = L.lqs_plan_fused(n, "c128", c.ops, best)[0]
+    assert n_seg >= 1
