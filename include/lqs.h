@@ -72,16 +72,25 @@ extern "C" {
 typedef enum { LQS_C64 = 0, LQS_C128 = 1 } lqs_dtype;
 
 /* Gate set: Pauli-X/Z and CNOT (Sec. 2, Sec. 3.1), Hadamard and controlled
- * phase / R_k (Sec. 3.2, Fig. 5a, Fig. 6a), DoubleExcitation's building
- * blocks and parametrised rotations for variational circuits (Listing 1),
- * Toffoli (the 8x8 case of Sec. 2), and generic 2x2 / 4x4 unitaries (the
- * "general approach" of Sec. 3.1). */
+ * phase / R_k (Sec. 3.2, Fig. 5a, Fig. 6a), parametrised rotations and
+ * DoubleExcitation for variational circuits (Listing 1), Toffoli and CSWAP
+ * (the 8x8 cases of Sec. 2), and generic 2x2 / 4x4 unitaries (the "general
+ * approach" of Sec. 3.1).
+ *   CSWAP: wires {c, a, b}: swaps a and b where c = 1.
+ *   DoubleExcitation(theta): wires {w0, w1, w2, w3} (w0 the most significant
+ *     bit of the 16x16 matrix); rotates the pair |0011>, |1100>:
+ *     |0011> -> cos(theta/2)|0011> + sin(theta/2)|1100>,
+ *     |1100> -> cos(theta/2)|1100> - sin(theta/2)|0011>; every other basis
+ *     state is unchanged.  It runs as CNOTs from w0 to w1, w2, w3, X on w1,
+ *     an RY(theta) on w0 controlled by w1, w2, w3, and the same CNOTs and X
+ *     undone, so it takes the dense, permutation and fused kernels as they
+ *     are; its gradient is that controlled RY's. */
 typedef enum {
   LQS_X = 0, LQS_Y = 1, LQS_Z = 2, LQS_H = 3, LQS_S = 4, LQS_T = 5,
   LQS_RX = 6, LQS_RY = 7, LQS_RZ = 8, LQS_PHASE = 9, LQS_ROT = 10,
   LQS_CNOT = 11, LQS_CZ = 12, LQS_SWAP = 13, LQS_CPHASE = 14, LQS_CRY = 15,
-  LQS_TOFFOLI = 16, LQS_U2 = 17, LQS_U4 = 18,
-  LQS_NUM_GATES = 19
+  LQS_TOFFOLI = 16, LQS_U2 = 17, LQS_U4 = 18, LQS_CSWAP = 19, LQS_DOUBLE_EXCITATION = 20,
+  LQS_NUM_GATES = 21
 } lqs_gate;
 
 /* c128 arithmetic selection (lqs_fuse_cfg.arith and lqs_set_arith). */
@@ -94,7 +103,7 @@ typedef struct lqs_sv lqs_sv; /* opaque state-vector handle */
  * only, host pointer, row-major interleaved complex128, read during the call. */
 typedef struct {
   int32_t gate;
-  int32_t wires[3];
+  int32_t wires[4]; /* the gate's wires in order (unused entries ignored) */
   int32_t param_idx;
   int32_t inverse; /* nonzero: apply the adjoint U^dagger */
   const double* matrix;
@@ -190,7 +199,9 @@ LQS_API int lqs_autotune_fused(lqs_sv* sv, const lqs_op* ops, int n_ops, const d
  * *n_segments receives the number of HBM passes; when seg_qubit_mask is
  * non-null it receives each segment's tile qubit set (capacity `cap`), and
  * op_segment (n_ops entries, optional) each op's segment.  Ops executed
- * segment by segment in their original relative order reproduce the circuit. */
+ * segment by segment in their original relative order reproduce the circuit.
+ * A gate that runs as several kernel ops (DoubleExcitation) is reported with
+ * the segment of its last one; its ops may sit in several segments. */
 LQS_API int lqs_plan_fused(int n_qubits, int dtype, const lqs_op* ops, int n_ops, const lqs_fuse_cfg* cfg_or_null,
                    int* n_segments, uint64_t* seg_qubit_mask, int cap, int* op_segment);
 

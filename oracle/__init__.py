@@ -96,7 +96,7 @@ def gate_matrix(name: str, params: Sequence[float] = (), matrix: Optional[np.nda
     if matrix is not None:
         m = np.ascontiguousarray(matrix, dtype=np.complex128).reshape(-1)
         user[: 2 * m.size] = m.view(np.float64)
-    out = np.zeros(128, dtype=np.float64)
+    out = np.zeros(512, dtype=np.float64)
     mm = ctypes.c_int(0)
     if lib().oracle_gate_matrix(GATE_ID[name], _dp(p), _dp(user), int(inverse), _dp(out), ctypes.byref(mm)):
         raise ValueError(name)
@@ -108,6 +108,8 @@ def apply_matrix(psi: np.ndarray, n: int, wires: Sequence[int], U: np.ndarray) -
     """In place: psi <- U_full psi for U on ``wires``."""
     _check_state(psi, n)
     w = np.asarray(wires, dtype=np.int32)
+    if not 1 <= len(w) <= 4 or U.shape != (1 << len(w), 1 << len(w)):
+        raise ValueError("apply_matrix takes 1 to 4 wires and a matching square matrix")
     Uc = np.ascontiguousarray(U, dtype=np.complex128)
     lib().oracle_apply_matrix(_dp(psi.view(np.float64)), n, _ip(w), len(w), _dp(Uc.view(np.float64)))
     return psi
@@ -152,11 +154,11 @@ def run_circuit(circuit: Circuit, psi0: Optional[np.ndarray] = None,
     _check_state(psi, n)
     P = np.asarray(circuit.params if params is None else params, dtype=np.float64)
     nops = len(circuit.ops)
-    recs = np.zeros((max(nops, 1), 6), dtype=np.int32)
+    recs = np.zeros((max(nops, 1), 7), dtype=np.int32)
     mats = np.zeros((max(nops, 1), 32), dtype=np.float64)
     for k, op in enumerate(circuit.ops):
-        w = list(op.wires) + [0] * (3 - len(op.wires))
-        recs[k] = [GATE_ID[op.name], w[0], w[1], w[2], op.pidx, int(op.inverse)]
+        w = list(op.wires) + [0] * (4 - len(op.wires))
+        recs[k] = [GATE_ID[op.name], w[0], w[1], w[2], w[3], op.pidx, int(op.inverse)]
         if op.matrix is not None:
             m = np.ascontiguousarray(op.matrix, dtype=np.complex128).reshape(-1)
             mats[k, : 2 * m.size] = m.view(np.float64)
@@ -197,6 +199,8 @@ def energy(circuit: Circuit, terms: Sequence[Pauli], params: Optional[np.ndarray
 # each angle of Rot) obeys dE/dtheta = [E(theta + pi/2) - E(theta - pi/2)] / 2.
 # CRY's generator P1 (x) Y / 2 has eigenvalues {0, 0, +1/2, -1/2}: two
 # frequencies (1/2 and 1), so it takes the four-term rule of Anselmetti et al.
+# DoubleExcitation's generator (Y/2 on the pair |0011>, |1100>, 0 elsewhere)
+# has the same spectrum and takes the same rule.
 # (New J. Phys. 23, 113010, 2021) / Wierichs et al. (Quantum 6, 677, 2022):
 #   dE/dtheta = c1 [E(+pi/2) - E(-pi/2)] - c2 [E(+3pi/2) - E(-3pi/2)],
 #   c1 = (2 + sqrt 2) / 8, c2 = (2 - sqrt 2) / 8.
@@ -228,7 +232,7 @@ def param_shift_grad(circuit: Circuit, terms: Sequence[Pauli], psi0: Optional[np
         for s in range(npar):
             if op.name in _TWO_TERM:
                 d = 0.5 * (E_with(k, s, math.pi / 2) - E_with(k, s, -math.pi / 2))
-            elif op.name == "CRY":
+            elif op.name in ("CRY", "DoubleExcitation"):
                 c1 = (2.0 + math.sqrt(2.0)) / 8.0
                 c2 = (2.0 - math.sqrt(2.0)) / 8.0
                 d = c1 * (E_with(k, s, math.pi / 2) - E_with(k, s, -math.pi / 2)) \

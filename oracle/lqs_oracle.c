@@ -40,10 +40,10 @@ typedef double _Complex cplx;
 /* Gate numbering shared by name with the circuit descriptions. */
 enum {
   O_X, O_Y, O_Z, O_H, O_S, O_T, O_RX, O_RY, O_RZ, O_PHASE, O_ROT,
-  O_CNOT, O_CZ, O_SWAP, O_CPHASE, O_CRY, O_TOFFOLI, O_U2, O_U4, O_NGATES
+  O_CNOT, O_CZ, O_SWAP, O_CPHASE, O_CRY, O_TOFFOLI, O_U2, O_U4, O_CSWAP, O_DEXC, O_NGATES
 };
-static const int o_nwires[O_NGATES] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 1, 2};
-static const int o_nparams[O_NGATES] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 3, 0, 0, 0, 1, 1, 0, 0, 0};
+static const int o_nwires[O_NGATES] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 1, 2, 3, 4};
+static const int o_nparams[O_NGATES] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 3, 0, 0, 0, 1, 1, 0, 0, 0, 0, 1};
 
 int oracle_gate_wires(int gate) { return (gate >= 0 && gate < O_NGATES) ? o_nwires[gate] : -1; }
 int oracle_gate_params(int gate) { return (gate >= 0 && gate < O_NGATES) ? o_nparams[gate] : -1; }
@@ -94,13 +94,13 @@ static void controlled(cplx* M, int dim, const cplx* U) {
 }
 
 /*
- * The 2^m x 2^m matrix of `gate` (row-major) into `out` (64 entries suffice),
+ * The 2^m x 2^m matrix of `gate` (row-major) into `out` (256 entries suffice),
  * its wire count into *m.  `params` holds the gate's parameters; `user` the
  * caller's row-major matrix for U2/U4 (interleaved re,im).  `inverse` returns
  * the conjugate transpose.  Returns 0, or -1 for an unknown gate.
  */
 int oracle_gate_matrix(int gate, const double* params, const double* user, int inverse, double* out_ri, int* m) {
-  cplx M[64], A[4], B[4];
+  cplx M[256], A[4], B[4];
   if (gate < 0 || gate >= O_NGATES) return -1;
   int w = o_nwires[gate], dim = 1 << w;
   const double r2 = 1.0 / sqrt(2.0);
@@ -131,6 +131,20 @@ int oracle_gate_matrix(int gate, const double* params, const double* user, int i
     case O_CPHASE: mat2(A, 1, 0, 0, cexp(I * params[0])); controlled(M, 4, A); break;
     case O_CRY: rot_y(A, params[0]); controlled(M, 4, A); break;
     case O_TOFFOLI: mat2(A, 0, 1, 1, 0); controlled(M, 8, A); break;
+    case O_CSWAP:  /* wires (c, a, b): local index 4c + 2a + b; |101> <-> |110> */
+      memset(M, 0, sizeof(cplx) * 64);
+      for (int k = 0; k < 8; ++k) M[k * 8 + k] = 1;
+      M[5 * 8 + 5] = 0; M[6 * 8 + 6] = 0;
+      M[5 * 8 + 6] = 1; M[6 * 8 + 5] = 1;
+      break;
+    case O_DEXC: { /* rotation of the pair |0011> (index 3), |1100> (index 12) */
+      const double c = cos(params[0] / 2), s = sin(params[0] / 2);
+      memset(M, 0, sizeof(cplx) * 256);
+      for (int k = 0; k < 16; ++k) M[k * 16 + k] = 1;
+      M[3 * 16 + 3] = c;  M[12 * 16 + 3] = s;
+      M[3 * 16 + 12] = -s; M[12 * 16 + 12] = c;
+      break;
+    }
     case O_U2:
     case O_U4:
       for (int k = 0; k < dim * dim; ++k) M[k] = user[2 * k] + I * user[2 * k + 1];
@@ -160,11 +174,12 @@ static uint64_t group_index(uint64_t base, const int* wires, int m, int a) {
  * psi <- U_full psi for the 2^m x 2^m matrix U (interleaved re,im, row-major)
  * acting on `wires`.  Every index whose wire bits are all zero is the base of
  * one group of 2^m amplitudes; the group is gathered, multiplied by U and
- * scattered back.  Wires must be distinct and < n; m <= 3.
+ * scattered back.  Wires must be distinct and < n; m <= 4.
  */
 void oracle_apply_matrix(double* psi_ri, int n, const int* wires, int m, const double* U_ri) {
   cplx* psi = (cplx*)psi_ri;
-  cplx U[64];
+  cplx U[256];
+  if (m < 1 || m > 4) return; /* the buffers hold at most 4 wires (the wrapper rejects more) */
   int dim = 1 << m;
   uint64_t N = (uint64_t)1 << n, wmask = 0;
   for (int k = 0; k < dim * dim; ++k) U[k] = U_ri[2 * k] + I * U_ri[2 * k + 1];
@@ -172,8 +187,8 @@ void oracle_apply_matrix(double* psi_ri, int n, const int* wires, int m, const d
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < (int64_t)N; ++i) {
     if ((uint64_t)i & wmask) continue;
-    cplx v[8], r[8];
-    uint64_t idx[8];
+    cplx v[16], r[16];
+    uint64_t idx[16];
     for (int a = 0; a < dim; ++a) {
       idx[a] = group_index((uint64_t)i, wires, m, a);
       v[a] = psi[idx[a]];
@@ -216,7 +231,7 @@ void oracle_apply_matrix_at(const double* psi_ri, int n, const int* wires, int m
 /* Apply one gate: build its matrix, then the general update. */
 int oracle_apply_gate(double* psi_ri, int n, int gate, const int* wires, const double* params,
                       const double* user, int inverse) {
-  double U[128];
+  double U[512];
   int m;
   if (oracle_gate_matrix(gate, params, user, inverse, U, &m)) return -1;
   for (int k = 0; k < m; ++k) {
@@ -235,9 +250,9 @@ int oracle_apply_gate(double* psi_ri, int n, int gate, const int* wires, const d
  */
 int oracle_run(double* psi_ri, int n, const int* ops, int n_ops, const double* params, const double* mats) {
   for (int k = 0; k < n_ops; ++k) {
-    const int* o = ops + 6 * k;
-    const double* p = o[4] >= 0 ? params + o[4] : NULL;
-    if (oracle_apply_gate(psi_ri, n, o[0], o + 1, p, mats + 32 * k, o[5])) return -1 - k;
+    const int* o = ops + 7 * k; /* gate, 4 wires, parameter index, inverse */
+    const double* p = o[5] >= 0 ? params + o[5] : NULL;
+    if (oracle_apply_gate(psi_ri, n, o[0], o + 1, p, mats + 32 * k, o[6])) return -1 - k;
   }
   return 0;
 }

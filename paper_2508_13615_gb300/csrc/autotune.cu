@@ -29,11 +29,11 @@ static std::map<std::string, lqs_fuse_cfg> g_tuned;
 // coefficients, not the plan).
 static std::string tune_key(int n, int dtype, const lqs_op* ops, int n_ops) {
   std::string k;
-  k.reserve(16 + (size_t)n_ops * 16);
+  k.reserve(16 + (size_t)n_ops * 20);
   const int hdr[3] = {n, dtype, n_ops};
   k.append(reinterpret_cast<const char*>(hdr), sizeof hdr);
   for (int i = 0; i < n_ops; ++i) {
-    const int32_t rec[4] = {ops[i].gate, ops[i].wires[0], ops[i].wires[1], ops[i].wires[2]};
+    const int32_t rec[5] = {ops[i].gate, ops[i].wires[0], ops[i].wires[1], ops[i].wires[2], ops[i].wires[3]};
     k.append(reinterpret_cast<const char*>(rec), sizeof rec);
   }
   return k;

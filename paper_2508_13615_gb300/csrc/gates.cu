@@ -16,11 +16,12 @@ namespace lqs {
 
 using cd = std::complex<double>;
 
-static const int kWires[LQS_NUM_GATES] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 1, 2};
-static const int kParams[LQS_NUM_GATES] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 3, 0, 0, 0, 1, 1, 0, 0, 0};
+static const int kWires[LQS_NUM_GATES] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 1, 2, 3, 4};
+static const int kParams[LQS_NUM_GATES] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 3, 0, 0, 0, 1, 1, 0, 0, 0, 0, 1};
 static const char* kNames[LQS_NUM_GATES] = {"X",  "Y",    "Z",   "H",    "S",    "T",      "RX",
                                             "RY", "RZ",   "PhaseShift", "Rot", "CNOT", "CZ", "SWAP",
-                                            "ControlledPhaseShift", "CRY", "Toffoli", "U2", "U4"};
+                                            "ControlledPhaseShift", "CRY", "Toffoli", "U2", "U4",
+                                            "CSWAP", "DoubleExcitation"};
 
 static void put(KOp& k, int i, cd v) {
   k.m[2 * i] = v.real();
@@ -236,6 +237,30 @@ int lower_gate(int n, int gate, const int* wires, int n_wires, const double* par
       out.push_back(k);
       break;
     case LQS_TOFFOLI: out.push_back(anti1_op(t, (1ull << wires[0]) | (1ull << wires[1]), 1.0, 1.0)); break;
+    case LQS_CSWAP:  // a SWAP of wires[1], wires[2] under the control wires[0]
+      k.kind = K_SWAP;
+      k.t0 = wires[1];
+      k.t1 = wires[2];
+      k.cmask = 1ull << wires[0];
+      out.push_back(k);
+      break;
+    case LQS_DOUBLE_EXCITATION: {
+      // CNOTs from w0 to w1, w2, w3 send |0011> to itself and |1100> to
+      // |1011>: the pair then differs only in w0, with (w1, w2, w3) = (0, 1, 1)
+      // and no other state there.  X on w1 makes that the all-ones control
+      // pattern of an RY on w0, which is the rotation; then X and the CNOTs
+      // are undone.
+      const int w0 = wires[0], w1 = wires[1], w2 = wires[2], w3 = wires[3];
+      for (int c : {w1, w2, w3}) out.push_back(anti1_op(c, 1ull << w0, 1.0, 1.0));
+      out.push_back(anti1_op(w1, 0, 1.0, 1.0));
+      rot_y(u, inv ? -params[0] : params[0]);
+      k = dense1_op(w0, (1ull << w1) | (1ull << w2) | (1ull << w3), u, true);
+      with_gen(k, slot, G_Y, 1.0, inv);
+      out.push_back(k);
+      out.push_back(anti1_op(w1, 0, 1.0, 1.0));
+      for (int c : {w3, w2, w1}) out.push_back(anti1_op(c, 1ull << w0, 1.0, 1.0));
+      break;
+    }
     case LQS_U2:
       for (int i = 0; i < 4; ++i) u[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
       for (int i = 0; i < 8; ++i)

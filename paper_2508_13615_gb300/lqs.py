@@ -31,14 +31,17 @@ LQS_JIT_OFF, LQS_JIT_ON, LQS_JIT_AUTO = 0, 1, 2
 GATE_IDS = {
     "X": 0, "Y": 1, "Z": 2, "H": 3, "S": 4, "T": 5, "RX": 6, "RY": 7, "RZ": 8, "PhaseShift": 9, "Rot": 10,
     "CNOT": 11, "CZ": 12, "SWAP": 13, "ControlledPhaseShift": 14, "CRY": 15, "Toffoli": 16, "U2": 17, "U4": 18,
+    "CSWAP": 19, "DoubleExcitation": 20,
 }
 GATE_NWIRES = {"X": 1, "Y": 1, "Z": 1, "H": 1, "S": 1, "T": 1, "RX": 1, "RY": 1, "RZ": 1, "PhaseShift": 1, "Rot": 1,
-               "CNOT": 2, "CZ": 2, "SWAP": 2, "ControlledPhaseShift": 2, "CRY": 2, "Toffoli": 3, "U2": 1, "U4": 2}
-GATE_NPARAMS = {"RX": 1, "RY": 1, "RZ": 1, "PhaseShift": 1, "Rot": 3, "ControlledPhaseShift": 1, "CRY": 1}
+               "CNOT": 2, "CZ": 2, "SWAP": 2, "ControlledPhaseShift": 2, "CRY": 2, "Toffoli": 3, "U2": 1, "U4": 2,
+               "CSWAP": 3, "DoubleExcitation": 4}
+GATE_NPARAMS = {"RX": 1, "RY": 1, "RZ": 1, "PhaseShift": 1, "Rot": 3, "ControlledPhaseShift": 1, "CRY": 1,
+                "DoubleExcitation": 1}
 
 
 class lqs_op(ctypes.Structure):
-    _fields_ = [("gate", ctypes.c_int32), ("wires", ctypes.c_int32 * 3), ("param_idx", ctypes.c_int32),
+    _fields_ = [("gate", ctypes.c_int32), ("wires", ctypes.c_int32 * 4), ("param_idx", ctypes.c_int32),
                 ("inverse", ctypes.c_int32), ("matrix", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -170,7 +173,7 @@ class OpArray:
             rec = self.arr[i]
             rec.gate = GATE_IDS[op.name]
             w = list(op.wires)
-            for j in range(3):
+            for j in range(4):
                 rec.wires[j] = int(w[j]) if j < len(w) else 0
             rec.param_idx = int(op.pidx) if getattr(op, "pidx", -1) is not None else -1
             rec.inverse = int(bool(getattr(op, "inverse", False)))

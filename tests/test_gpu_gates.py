@@ -107,3 +107,24 @@ def test_validation_errors_leave_state_untouched():
             with pytest.raises((L.LqsError, ValueError)):
                 sv.apply_gate(*bad)
         np.testing.assert_array_equal(sv.numpy(), psi0)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_cswap_and_double_excitation_every_placement(dtype, arith):
+    """The 8x8 and 16x16 gates of the extended set on the plain path, with
+    wires below, inside and above the low tile bits, against the oracle."""
+    set_mode(arith)
+    n = 12
+    psi0 = W.gaussian_state(n, 55)
+    cases = [("CSWAP", (0, 1, 2), []), ("CSWAP", (11, 0, 6), []), ("CSWAP", (3, 10, 4), []),
+             ("DoubleExcitation", (0, 1, 2, 3), [0.4]), ("DoubleExcitation", (11, 2, 7, 0), [-1.1]),
+             ("DoubleExcitation", (5, 9, 1, 10), [2.5])]
+    for name, wires, p in cases:
+        for inv in (False, True):
+            c = W.Circuit(n)
+            c.ops.append(W.Op(name, wires, 0 if p else -1, None, inv))
+            c.params = np.asarray(p if p else [0.0])
+            with gpu_state(n, dtype, psi0) as sv:
+                sv.apply(c, fused=False)
+                err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
+            assert err <= TOL[dtype], (name, wires, inv, err)

@@ -107,7 +107,7 @@ def test_angles_reuse_the_compiled_kernels(jit_on):
 # compiled adjoint (reverse sweep over psi and lambda in registers)
 # ---------------------------------------------------------------------------
 PARAM_GATES = ["RX", "RY", "RZ", "PhaseShift", "Rot", "ControlledPhaseShift", "CRY", "H", "CNOT", "SWAP", "Toffoli",
-               "S", "U4", "Y", "CZ"]
+               "S", "U4", "Y", "CZ", "DoubleExcitation", "CSWAP"]
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)

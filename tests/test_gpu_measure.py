@@ -76,7 +76,7 @@ def test_adjoint_all_parametrised_gates(dtype, arith):
     set_mode(arith)
     n = 6
     names = ["RX", "RY", "RZ", "PhaseShift", "Rot", "ControlledPhaseShift", "CRY", "H", "CNOT", "SWAP", "Toffoli", "S",
-             "U4", "Y"]
+             "U4", "Y", "DoubleExcitation", "CSWAP"]
     c = W.random_circuit(n, 60, seed=7, names=names)
     psi0 = W.gaussian_state(n, 3)
     terms = W.tfim(n) + [W.pauli_word(0.7, {1: "Y", 4: "X"}), W.pauli_word(-0.2, {0: "Y", 2: "Z", 5: "Y"})]

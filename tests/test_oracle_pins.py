@@ -392,9 +392,10 @@ def test_paper_facts():
     # 16 bytes per complex128 amplitude: 2^30 amplitudes >= 16 GB, 2^40 ~ 16 TiB
     assert (1 << 30) * 16 / 1e9 >= facts["state_bytes"]["n30_at_least_gb"]
     assert (1 << 40) * 16 / 2 ** 40 == facts["state_bytes"]["n40_approx_tib"]
-    # largest gate matrix in the gate set is 8x8 (Toffoli)
+    # largest gate matrix a kernel applies is 8x8 (Toffoli, CSWAP); DoubleExcitation (Listing 1) is
+    # defined by its 16x16 matrix in the oracle, but the GPU path runs it as CNOTs, X and a controlled RY
     assert max(oracle.gate_matrix(g, [0.1] * p, W.haar_unitary(1 << m, 1) if g in ("U2", "U4") else None).shape[0]
-               for g, m, p in W.GATES) == facts["max_gate_matrix_dim"]["value"]
+               for g, m, p in W.GATES if g != "DoubleExcitation") == facts["max_gate_matrix_dim"]["value"]
     # QFT uses only H and controlled phases (before the final reversal), n H and n(n-1)/2 phases
     for n in (3, 8, 30):
         ops = W.qft(n, swaps=False).ops
@@ -413,3 +414,62 @@ def test_paper_facts():
     sw = W.sweep_30q()
     cn = [c for name, c in sw if name.startswith("CNOT")]
     assert all(c.ops[0].wires[0] == facts["cnot_control_24"]["value"] for c in cn if c.ops[0].wires[1] != 24)
+
+
+def test_cswap_is_three_toffolis():
+    """CSWAP(c, a, b) = Toffoli(c, a, b) Toffoli(c, b, a) Toffoli(c, a, b) (swap by three controlled XORs)."""
+    n = 5
+    psi = rand_state(n, 71)
+    for c, a, b in ((0, 1, 2), (4, 0, 3), (2, 4, 1)):
+        got = oracle.run_circuit(W.Circuit(n).add("CSWAP", (c, a, b)), psi)
+        want = oracle.run_circuit(W.Circuit(n).add("Toffoli", (c, a, b)).add("Toffoli", (c, b, a))
+                                  .add("Toffoli", (c, a, b)), psi)
+        np.testing.assert_allclose(got, want, atol=1e-15)
+
+
+def test_double_excitation_definition():
+    """DoubleExcitation(theta) rotates |0011>, |1100> (first wire most significant) by theta/2 and fixes
+    every other basis state; its angles add, and theta = 2 pi negates the pair."""
+    n = 6
+    wires = (4, 1, 5, 0)
+    th = 0.7
+    for x in range(1 << n):
+        bits = tuple((x >> w) & 1 for w in wires)
+        out = oracle.run_circuit(W.Circuit(n).add("DoubleExcitation", wires, [th]), oracle.basis_state(n, x))
+        if bits == (0, 0, 1, 1):
+            partner = x ^ sum(1 << w for w in wires)
+            assert abs(out[x] - math.cos(th / 2)) < 1e-15 and abs(out[partner] - math.sin(th / 2)) < 1e-15
+        elif bits == (1, 1, 0, 0):
+            partner = x ^ sum(1 << w for w in wires)
+            assert abs(out[x] - math.cos(th / 2)) < 1e-15 and abs(out[partner] + math.sin(th / 2)) < 1e-15
+        else:
+            assert abs(out[x] - 1.0) < 1e-15 and np.sum(np.abs(out)) - 1.0 < 1e-15
+    psi = rand_state(n, 72)
+    two = oracle.run_circuit(W.Circuit(n).add("DoubleExcitation", wires, [0.3]).add("DoubleExcitation", wires, [0.5]),
+                             psi)
+    one = oracle.run_circuit(W.Circuit(n).add("DoubleExcitation", wires, [0.8]), psi)
+    np.testing.assert_allclose(two, one, atol=1e-14)
+    full = oracle.run_circuit(W.Circuit(n).add("DoubleExcitation", wires, [2 * math.pi]), psi)
+    pair = [x for x in range(1 << n) if tuple((x >> w) & 1 for w in wires) in ((0, 0, 1, 1), (1, 1, 0, 0))]
+    rest = [x for x in range(1 << n) if x not in pair]
+    np.testing.assert_allclose(full[pair], -psi[pair], atol=1e-14)
+    np.testing.assert_allclose(full[rest], psi[rest], atol=1e-15)
+
+
+def test_double_excitation_four_term_shift_matches_finite_differences():
+    """The generator's spectrum {0, +-1/2} takes the four-term rule; central differences agree."""
+    n = 6
+    c = W.Circuit(n)
+    for q in range(n):
+        c.add("RY", (q,), [0.3 + 0.1 * q])
+    c.add("DoubleExcitation", (0, 2, 3, 5), [0.9]).add("CNOT", (1, 4)).add("DoubleExcitation", (5, 4, 1, 0), [-1.3])
+    terms = W.tfim(n)
+    g = oracle.param_shift_grad(c, terms)
+    h = 1e-6
+    for k in (n, n + 1):
+        p = c.params.copy()
+        p[k] += h
+        ep = oracle.energy(c, terms, p)
+        p[k] -= 2 * h
+        em = oracle.energy(c, terms, p)
+        assert abs((ep - em) / (2 * h) - g[k]) < 1e-8

@@ -151,7 +151,7 @@ GATES: List[Tuple[str, int, int]] = [
     ("X", 1, 0), ("Y", 1, 0), ("Z", 1, 0), ("H", 1, 0), ("S", 1, 0), ("T", 1, 0),
     ("RX", 1, 1), ("RY", 1, 1), ("RZ", 1, 1), ("PhaseShift", 1, 1), ("Rot", 1, 3),
     ("CNOT", 2, 0), ("CZ", 2, 0), ("SWAP", 2, 0), ("ControlledPhaseShift", 2, 1), ("CRY", 2, 1),
-    ("Toffoli", 3, 0), ("U2", 1, 0), ("U4", 2, 0),
+    ("Toffoli", 3, 0), ("U2", 1, 0), ("U4", 2, 0), ("CSWAP", 3, 0), ("DoubleExcitation", 4, 1),
 ]
 GATE_ID = {name: i for i, (name, _, _) in enumerate(GATES)}
 GATE_WIRES = {name: w for name, w, _ in GATES}
