@@ -96,6 +96,7 @@ class SegGen {
   std::ostringstream pre_;  // before the tile loop (tile-independent per-thread values)
   std::string why_;
   std::vector<std::pair<std::string, int>> pend_;  // gradient partials awaiting a batched warp sum
+  int ntab_ = 0;  // entries of the shared table of outside-qubit factor products
 
   int nthreads() const { return 1 << (k_ - r_); }
   void flush_pending(bool all);
@@ -675,12 +676,31 @@ bool SegGen::emit_op(const TOp& t) {
       }
       const std::string a = fresh("a");
       o_ << "      C " << a << " = " << h << ";\n";
-      int j = 0;
-      for (int q = 0; q < 64; ++q) {
-        if (!((EF >> q) & 1ull)) continue;
-        o_ << "      if ((base >> " << q << ") & 1ull) " << a << " = A::kmul("
-           << cref(c + 1 + __builtin_popcount(LF) + j) << ", " << a << ");\n";
-        ++j;
+      // factors on qubits outside the tile depend only on the tile: groups of
+      // up to 4 such qubits get a 16-entry product table in shared memory,
+      // filled once per CTA before the tile loop (its first barrier orders the
+      // fill before any use), so a tile pays one product per group
+      std::vector<std::pair<int, int>> outs;  // (qubit, coefficient index)
+      for (int q = 0, j = 0; q < 64; ++q)
+        if ((EF >> q) & 1ull) outs.emplace_back(q, c + 1 + __builtin_popcount(LF) + j++);
+      for (size_t g0 = 0; g0 < outs.size(); g0 += 4) {
+        const size_t m = std::min<size_t>(4, outs.size() - g0);
+        if (m == 1) {
+          o_ << "      if ((base >> " << outs[g0].first << ") & 1ull) " << a << " = A::kmul(" << cref(outs[g0].second)
+             << ", " << a << ");\n";
+          continue;
+        }
+        const int off = ntab_;
+        ntab_ += 1 << m;
+        pre_ << "  for (uint32_t i = tid; i < " << (1u << m) << "u; i += blockDim.x) {\n    C f = A::cconst1();\n";
+        for (size_t b = 0; b < m; ++b)
+          pre_ << "    if (i & " << (1u << b) << "u) f = A::kmul(" << cref(outs[g0 + b].second) << ", f);\n";
+        pre_ << "    TBL[" << off << "u + i] = f;\n  }\n";
+        std::string ix;
+        for (size_t b = 0; b < m; ++b)
+          ix += std::string(b ? " | " : "") + "((uint32_t)(base >> " + std::to_string(outs[g0 + b].first) + ") & 1u) << " +
+                std::to_string(b);
+        o_ << "      " << a << " = A::kmul(TBL[" << off << "u + (" << ix << ")], " << a << ");\n";
       }
       uint32_t fmask = 0;  // register slots carrying a factor
       for (int m = 0; m < r_; ++m)
@@ -749,7 +769,7 @@ extern "C" __global__ void __launch_bounds__(@NTH@, @MINB@)
 @LAMCOPY0@  }
   uint32_t phase = 0;
   bool ok = true;
-@PRE@  for (; t < G.ntiles; t += gridDim.x) {
+@TBL@@PRE@  for (; t < G.ntiles; t += gridDim.x) {
     const uint64_t base = lqs::tile_base(G, t);
     ok = __syncthreads_and(lqs::mbar_wait(bar, phase));
     phase ^= 1u;
@@ -909,6 +929,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   head = replace_all(head, "@NWACC@", std::to_string(adj_ ? nwarps * kMaxGradSlotsJit : 0) + "u");
   head = replace_all(head, "@LAMCOPY0@",
                      adj_ ? "    lqs::jit::seg_copy(G, S0L, lam, lqs::tile_base(G, t), bar, my_roff);\n" : "");
+  head = replace_all(head, "@TBL@", ntab_ ? "  __shared__ C TBL[" + std::to_string(ntab_) + "];\n" : std::string());
   head = replace_all(head, "@PRE@", pre_.str());
   std::string tail = kSkeletonTail;
   std::string gout;
