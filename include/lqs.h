@@ -154,6 +154,12 @@ LQS_API int lqs_sv_copy_from_host(lqs_sv* sv, const void* host);
 /* Copy the state to host memory; returns when the data is in `host`. */
 LQS_API int lqs_sv_copy_to_host(const lqs_sv* sv, void* host);
 
+/* The same copy, only enqueued on the state's stream: `host` (pinned memory
+ * for the copy to overlap other work) holds the state once the stream has
+ * passed the copy, e.g. after lqs_sv_sync.  Lets a caller read a result back
+ * while other states are being computed on other streams. */
+LQS_API int lqs_sv_copy_to_host_async(const lqs_sv* sv, void* host);
+
 /* Wait for all work enqueued on the state's stream; reports deferred kernel
  * errors (LQS_ERR_CUDA) and device-side wait timeouts (LQS_ERR_TIMEOUT). */
 LQS_API int lqs_sv_sync(lqs_sv* sv);

@@ -364,6 +364,14 @@ int lqs_sv_copy_to_host(const lqs_sv* h, void* host) {
   return LQS_OK;
 }
 
+int lqs_sv_copy_to_host_async(const lqs_sv* h, void* host) {
+  LQS_TRY(check_sv(h));
+  if (!host) return set_error(LQS_ERR_ARG, "host is NULL");
+  const SV* sv = S_(h);
+  LQS_CUDA_TRY(cudaMemcpyAsync(host, sv->d, sv->bytes(), cudaMemcpyDeviceToHost, sv->stream));
+  return LQS_OK;
+}
+
 int lqs_sv_sync(lqs_sv* h) {
   LQS_TRY(check_sv(h));
   SV* sv = S_(h);

@@ -92,6 +92,7 @@ def _load():
         "lqs_sv_set_basis": (i32, [vp, u64]),
         "lqs_sv_copy_from_host": (i32, [vp, vp]),
         "lqs_sv_copy_to_host": (i32, [vp, vp]),
+        "lqs_sv_copy_to_host_async": (i32, [vp, vp]),
         "lqs_sv_sync": (i32, [vp]),
         "lqs_apply_gate": (i32, [vp, i32, ip, i32, dp, i32, i32]),
         "lqs_apply_matrix": (i32, [vp, ip, i32, dp]),
@@ -255,6 +256,14 @@ def lqs_sv_copy_to_host(h, host: np.ndarray) -> np.ndarray:
     if not host.flags.c_contiguous:
         raise ValueError("host buffer must be contiguous")
     _check(_L.lqs_sv_copy_to_host(h, host.ctypes.data))
+    return host
+
+
+def lqs_sv_copy_to_host_async(h, host: np.ndarray) -> np.ndarray:
+    """Enqueues the copy only; ``host`` holds the state after lqs_sv_sync(h)."""
+    if not host.flags.c_contiguous:
+        raise ValueError("host buffer must be contiguous")
+    _check(_L.lqs_sv_copy_to_host_async(h, host.ctypes.data))
     return host
 
 

@@ -128,3 +128,36 @@ def test_cswap_and_double_excitation_every_placement(dtype, arith):
                 sv.apply(c, fused=False)
                 err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
             assert err <= TOL[dtype], (name, wires, inv, err)
+
+
+def test_copies_on_other_streams_through_aliased_handles():
+    """Handles that share one device buffer but order their calls on different
+    streams: an upload on one stream, gates on another, an asynchronous
+    read-back on a third, chained by events; the host copy equals the oracle."""
+    import torch
+
+    import paper_2508_13615_gb300 as L
+    set_mode("df")
+    n = 14
+    psi0 = W.gaussian_state(n, 9)
+    c = W.ansatz(n, 2, 3)
+    want = oracle.run_circuit(c, psi0)
+    buf = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    s_up, s_run, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    up = L.StateVector(n, "c128", tensor=buf, stream=s_up)
+    run = L.StateVector(n, "c128", tensor=buf, stream=s_run)
+    down = L.StateVector(n, "c128", tensor=buf, stream=s_down)
+    host_in = torch.from_numpy(psi0.astype(np.complex128)).pin_memory().numpy()
+    host_out = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True).numpy()
+    e_up, e_run = torch.cuda.Event(), torch.cuda.Event()
+    L.lqs_sv_copy_from_host(up.h, host_in)
+    e_up.record(s_up)
+    s_run.wait_event(e_up)
+    run.apply(c, fused=False)
+    e_run.record(s_run)
+    s_down.wait_event(e_run)
+    L.lqs_sv_copy_to_host_async(down.h, host_out)
+    L.lqs_sv_sync(down.h)
+    assert max_abs(host_out, want) <= TOL["c128"]
+    for sv in (up, run, down):
+        sv.close()
