@@ -216,12 +216,15 @@ class E2EPipeline:
 
 # Peaks derived from the unit counts and clocks of the part (152 SMs, 128 FP32
 # lanes per SM, 2.07 GHz maximum SM clock): 40.3 T FP32 instructions/s.  The
-# double-float complex128 gate math costs about 6.3 FP32 instructions per
-# float64-equivalent flop (a real 2x2 or a complex scale: 38 instructions for
-# 6 flops per amplitude), so its arithmetic peak is 40.3 / 6.3 = 6.4 TFLOP/s
-# float64-equivalent; native complex64 math is 2 flops per FMA lane-cycle.
+# double-float complex128 gate math of the compiled segments costs 32 FP32
+# instructions per amplitude for a real 2x2 (6 flops): each of the two real
+# outputs is two products with their exact error terms (8), one TwoSum (6)
+# and two error additions, renormalised only every 16 updates.  That is 5.33
+# instructions per float64-equivalent flop, so the arithmetic peak is
+# 40.3 / 5.33 = 7.6 TFLOP/s float64-equivalent; native complex64 math is 2
+# flops per FMA lane-cycle.
 FP32_INSTR_PEAK = 152 * 128 * 2.07e9
-DF_INSTR_PER_FLOP = 38.0 / 6.0
+DF_INSTR_PER_FLOP = 32.0 / 6.0
 ALU_PEAK_TFLOPS = {"df": FP32_INSTR_PEAK / DF_INSTR_PER_FLOP / 1e12, "f32": 2 * FP32_INSTR_PEAK / 1e12,
                    "f64": 1.25}
 

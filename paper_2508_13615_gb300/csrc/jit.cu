@@ -58,6 +58,12 @@ uint32_t host_swz(uint32_t j, int sz) {
 }
 
 constexpr int kMaxGradSlotsJit = 128;  // gradient slots per compiled adjoint segment
+// Amplitude updates between renormalisations of the double-float registers.
+// The updates leave their results unrenormalised (jit_dev.cuh), and the low
+// parts grow with each one; a host simulation of 3000 random gates on 12
+// qubits kept the error of normalised double-float (2.5e-14) with up to 32
+// updates between renormalisations, and 2-5x that at 64-128.
+constexpr int kRenormEvery = 16;
 
 std::string hex(uint64_t x) {
   char b[32];
@@ -97,6 +103,7 @@ class SegGen {
   std::string why_;
   std::vector<std::pair<std::string, int>> pend_;  // gradient partials awaiting a batched warp sum
   int ntab_ = 0;  // entries of the shared table of outside-qubit factor products
+  int lz_ = 0;    // amplitude updates since the registers were last renormalised
 
   int nthreads() const { return 1 << (k_ - r_); }
   void flush_pending(bool all);
@@ -489,7 +496,7 @@ bool SegGen::emit_op(const TOp& t) {
             case 1: o_ << "      " << v << " = A::neg(" << v << ");\n"; break;
             case 2: o_ << "      " << v << " = A::mul_i(" << v << ");\n"; break;
             case 3: o_ << "      " << v << " = A::neg(A::mul_i(" << v << "));\n"; break;
-            default: o_ << "      " << v << " = A::cmul(" << cref(c) << ", " << v << ");\n"; break;
+            default: o_ << "      " << v << " = lqs::jit::Lz<A>::cmul(" << cref(c) << ", " << v << ");\n"; break;
           }
         }
       });
@@ -504,7 +511,7 @@ bool SegGen::emit_op(const TOp& t) {
       if (m >= 0) {
         each([&]() {
           for (int e = 0; e < R_; ++e)
-            if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << cref(c + ((e >> m) & 1)) << ", " << V(e) << ");\n";
+            if (qual(e)) o_ << "      " << V(e) << " = lqs::jit::Lz<A>::cmul(" << cref(c + ((e >> m) & 1)) << ", " << V(e) << ");\n";
         });
       } else {
         const std::string d = fresh("d");
@@ -513,7 +520,7 @@ bool SegGen::emit_op(const TOp& t) {
         o_ << "      const C " << d << " = " << bit << " ? " << cref(c + 1) << " : " << cref(c) << ";\n";
         each([&]() {
           for (int e = 0; e < R_; ++e)
-            if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << d << ", " << V(e) << ");\n";
+            if (qual(e)) o_ << "      " << V(e) << " = lqs::jit::Lz<A>::cmul(" << d << ", " << V(e) << ");\n";
         });
       }
       if (!p.empty()) o_ << "    }\n";
@@ -555,7 +562,7 @@ bool SegGen::emit_op(const TOp& t) {
       }
       each([&]() {
         for (int e = 0; e < R_; ++e)
-          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << fac[e] << ", " << V(e) << ");\n";
+          if (qual(e)) o_ << "      " << V(e) << " = lqs::jit::Lz<A>::cmul(" << fac[e] << ", " << V(e) << ");\n";
       });
       if (!p.empty()) o_ << "    }\n";
       return true;
@@ -591,8 +598,8 @@ bool SegGen::emit_op(const TOp& t) {
           for (int e = 0; e < R_; ++e) {
             if ((e >> m) & 1 || !qual(e)) continue;
             const int a = e, b = e | (1 << m);
-            o_ << "    " << V(b) << " = A::cmul(" << cref(c) << ", " << V(b) << ");\n";
-            o_ << "    " << V(a) << " = A::cmul(" << cref(c + 1) << ", " << V(a) << ");\n";
+            o_ << "    " << V(b) << " = lqs::jit::Lz<A>::cmul(" << cref(c) << ", " << V(b) << ");\n";
+            o_ << "    " << V(a) << " = lqs::jit::Lz<A>::cmul(" << cref(c + 1) << ", " << V(a) << ");\n";
           }
         });
         for (int e = 0; e < R_; ++e)
@@ -686,7 +693,7 @@ bool SegGen::emit_op(const TOp& t) {
       for (size_t g0 = 0; g0 < outs.size(); g0 += 4) {
         const size_t m = std::min<size_t>(4, outs.size() - g0);
         if (m == 1) {
-          o_ << "      if ((base >> " << outs[g0].first << ") & 1ull) " << a << " = A::kmul(" << cref(outs[g0].second)
+          o_ << "      if ((base >> " << outs[g0].first << ") & 1ull) " << a << " = lqs::jit::Lz<A>::kmul(" << cref(outs[g0].second)
              << ", " << a << ");\n";
           continue;
         }
@@ -700,7 +707,7 @@ bool SegGen::emit_op(const TOp& t) {
         for (size_t b = 0; b < m; ++b)
           ix += std::string(b ? " | " : "") + "((uint32_t)(base >> " + std::to_string(outs[g0 + b].first) + ") & 1u) << " +
                 std::to_string(b);
-        o_ << "      " << a << " = A::kmul(TBL[" << off << "u + (" << ix << ")], " << a << ");\n";
+        o_ << "      " << a << " = lqs::jit::Lz<A>::kmul(TBL[" << off << "u + (" << ix << ")], " << a << ");\n";
       }
       uint32_t fmask = 0;  // register slots carrying a factor
       for (int m = 0; m < r_; ++m)
@@ -721,12 +728,12 @@ bool SegGen::emit_op(const TOp& t) {
       for (uint32_t key : all) {
         const int m = 31 - __builtin_clz(key);
         const std::string nm = fresh("f");
-        o_ << "      const C " << nm << " = A::kmul(" << cref(lidx(slot_[m])) << ", " << tab[key ^ (1u << m)] << ");\n";
+        o_ << "      const C " << nm << " = lqs::jit::Lz<A>::kmul(" << cref(lidx(slot_[m])) << ", " << tab[key ^ (1u << m)] << ");\n";
         tab[key] = nm;
       }
       each([&]() {
         for (int e = 0; e < R_; ++e)
-          if (qual(e)) o_ << "      " << V(e) << " = A::cmul(" << tab[(uint32_t)e & fmask] << ", " << V(e) << ");\n";
+          if (qual(e)) o_ << "      " << V(e) << " = lqs::jit::Lz<A>::cmul(" << tab[(uint32_t)e & fmask] << ", " << V(e) << ");\n";
       });
       o_ << "    }\n";
       if (!p.empty()) o_ << "    }\n";
@@ -895,6 +902,16 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     if (!emit_op(ops[i])) {
       why = why_;
       return false;
+    }
+    const TOp& t = ops[i];
+    const bool plain = (t.kind == K_ANTI1 && t.special == 1) || (t.kind == K_PHASE && t.special != 0) ||
+                       t.kind == K_SWAP || t.kind == K_GRAD;
+    if (!plain && ++lz_ >= kRenormEvery) {
+      o_ << "    // renormalise the double-float registers\n";
+      each([&]() {
+        for (int e = 0; e < R_; ++e) o_ << "    lqs::jit::renorm<A>(" << V(e) << ");\n";
+      });
+      lz_ = 0;
     }
   }
   flush_pending(true);

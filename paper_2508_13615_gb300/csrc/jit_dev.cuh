@@ -14,6 +14,84 @@
 namespace lqs {
 namespace jit {
 
+// Amplitude updates of a compiled segment.  For double-float they return the
+// accumulator pair (leading sum, collected errors) without renormalising it:
+// that pair stands for the same value, and the next product, sum or float64
+// conversion takes it as it is (3 fewer float32 instructions per real
+// output).  The low parts then grow with every update, so the segment
+// renormalises every register after a bounded number of updates (renorm).
+// The other policies have no renormalisation to skip.
+template <class A> struct Lz {
+  using W = typename A::W;
+  using C = typename A::C;
+  using R = typename A::R;
+  static __device__ __forceinline__ W cmul(const C& c, const W& a) { return A::cmul(c, a); }
+  static __device__ __forceinline__ W cmac2(const C& c0, const W& a, const C& c1, const W& b) {
+    return A::cmac2(c0, a, c1, b);
+  }
+  static __device__ __forceinline__ W cmac4(const C* c, const W* a) { return A::cmac4(c, a); }
+  static __device__ __forceinline__ W rmac2(const R& c0, const W& a, const R& c1, const W& b) {
+    return A::rmac2(c0, a, c1, b);
+  }
+  static __device__ __forceinline__ C kmul(const C& a, const C& b) { return A::kmul(a, b); }
+  static __device__ __forceinline__ void renorm(W&) {}
+};
+template <> struct Lz<ArDF> {
+  using W = DFC;
+  using C = DFK;
+  static __device__ __forceinline__ DF raw(const DAcc& a) { return DF{a.s, a.e}; }
+  static __device__ __forceinline__ W cmul(const C& c, const W& a) {
+    DAcc re = df_prod(a.re, c.re);
+    df_mac(re, df_neg(a.im), c.im);
+    DAcc im = df_prod(a.im, c.re);
+    df_mac(im, a.re, c.im);
+    return W{raw(re), raw(im)};
+  }
+  static __device__ __forceinline__ W cmac2(const C& c0, const W& a, const C& c1, const W& b) {
+    DAcc re = df_prod(a.re, c0.re);
+    df_mac(re, df_neg(a.im), c0.im);
+    df_mac(re, b.re, c1.re);
+    df_mac(re, df_neg(b.im), c1.im);
+    DAcc im = df_prod(a.im, c0.re);
+    df_mac(im, a.re, c0.im);
+    df_mac(im, b.im, c1.re);
+    df_mac(im, b.re, c1.im);
+    return W{raw(re), raw(im)};
+  }
+  static __device__ __forceinline__ W cmac4(const C* c, const W* a) {
+    DAcc re = df_prod(a[0].re, c[0].re);
+    df_mac(re, df_neg(a[0].im), c[0].im);
+    DAcc im = df_prod(a[0].im, c[0].re);
+    df_mac(im, a[0].re, c[0].im);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      df_mac(re, a[k].re, c[k].re);
+      df_mac(re, df_neg(a[k].im), c[k].im);
+      df_mac(im, a[k].im, c[k].re);
+      df_mac(im, a[k].re, c[k].im);
+    }
+    return W{raw(re), raw(im)};
+  }
+  static __device__ __forceinline__ W rmac2(const DF& c0, const W& a, const DF& c1, const W& b) {
+    DAcc re = df_prod(a.re, c0);
+    df_mac(re, b.re, c1);
+    DAcc im = df_prod(a.im, c0);
+    df_mac(im, b.im, c1);
+    return W{raw(re), raw(im)};
+  }
+  static __device__ __forceinline__ C kmul(const C& a, const C& b) {
+    const W r = cmul(a, W{b.re, b.im});
+    return C{r.re, r.im};
+  }
+  static __device__ __forceinline__ void renorm(W& w) {
+    w.re = df_norm(DAcc{w.re.h, w.re.l});
+    w.im = df_norm(DAcc{w.im.h, w.im.l});
+  }
+};
+
+template <class A>
+__device__ __forceinline__ void renorm(typename A::W& a) { Lz<A>::renorm(a); }
+
 template <class A> struct Re;
 template <> struct Re<ArF32> { static __device__ __forceinline__ float get(const float2& c) { return c.x; } };
 template <> struct Re<ArF64> { static __device__ __forceinline__ double get(const double2& c) { return c.x; } };
@@ -24,8 +102,8 @@ template <class A>
 __device__ __forceinline__ void d1(typename A::W& a, typename A::W& b, const typename A::C& u00,
                                    const typename A::C& u01, const typename A::C& u10, const typename A::C& u11) {
   const typename A::W x = a, y = b;
-  a = A::cmac2(u00, x, u01, y);
-  b = A::cmac2(u10, x, u11, y);
+  a = Lz<A>::cmac2(u00, x, u01, y);
+  b = Lz<A>::cmac2(u10, x, u11, y);
 }
 
 // the same with a real matrix (real parts of the coefficients)
@@ -33,8 +111,8 @@ template <class A>
 __device__ __forceinline__ void d1r(typename A::W& a, typename A::W& b, const typename A::C& u00,
                                     const typename A::C& u01, const typename A::C& u10, const typename A::C& u11) {
   const typename A::W x = a, y = b;
-  a = A::rmac2(Re<A>::get(u00), x, Re<A>::get(u01), y);
-  b = A::rmac2(Re<A>::get(u10), x, Re<A>::get(u11), y);
+  a = Lz<A>::rmac2(Re<A>::get(u00), x, Re<A>::get(u01), y);
+  b = Lz<A>::rmac2(Re<A>::get(u10), x, Re<A>::get(u11), y);
 }
 
 // (x0..x3) <- U x with U row-major at u[0..15]
@@ -42,10 +120,10 @@ template <class A>
 __device__ __forceinline__ void d2(typename A::W& x0, typename A::W& x1, typename A::W& x2, typename A::W& x3,
                                    const typename A::C* u) {
   const typename A::W x[4] = {x0, x1, x2, x3};
-  x0 = A::cmac4(u, x);
-  x1 = A::cmac4(u + 4, x);
-  x2 = A::cmac4(u + 8, x);
-  x3 = A::cmac4(u + 12, x);
+  x0 = Lz<A>::cmac4(u, x);
+  x1 = Lz<A>::cmac4(u + 4, x);
+  x2 = Lz<A>::cmac4(u + 8, x);
+  x3 = Lz<A>::cmac4(u + 12, x);
 }
 
 // (a, b) <- (f0 b, f1 a)
@@ -53,8 +131,8 @@ template <class A>
 __device__ __forceinline__ void anti(typename A::W& a, typename A::W& b, const typename A::C& f0,
                                      const typename A::C& f1) {
   const typename A::W x = a;
-  a = A::cmul(f0, b);
-  b = A::cmul(f1, x);
+  a = Lz<A>::cmul(f0, b);
+  b = Lz<A>::cmul(f1, x);
 }
 
 // exchange a and b where p holds (a per-thread predicate)
