@@ -185,6 +185,14 @@ int add_tile_op(TileProg<A>& P, const KOp& o, int gslot) {
   t.coef = (int16_t)P.ncoef;
   for (int i = 0; i < nc; ++i) P.coef[P.ncoef + i] = (o.kind == K_DENSE1R) ? A::cconst(o.m[i], 0.0) : cc<A>(o, i);
   P.ncoef += nc;
+  // an uncontrolled real 2x2 with m11 = s m00 and m10 = -s m01 (s = +1:
+  // rotations such as RY, special 1; s = -1: reflections such as H, special 2)
+  // is g times an orthogonal matrix: compiled segments apply it in a cheaper
+  // form (the interpreter ignores the mark)
+  if (o.kind == K_DENSE1R && o.cmask == 0) {
+    if (o.m[3] == o.m[0] && o.m[2] == -o.m[1]) t.special = 1;
+    else if (o.m[3] == -o.m[0] && o.m[2] == o.m[1]) t.special = 2;
+  }
   P.op[P.nops++] = t;
   return LQS_OK;
 }

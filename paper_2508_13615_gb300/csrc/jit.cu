@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -104,6 +105,7 @@ class SegGen {
   std::vector<std::pair<std::string, int>> pend_;  // gradient partials awaiting a batched warp sum
   int ntab_ = 0;  // entries of the shared table of outside-qubit factor products
   int lz_ = 0;    // amplitude updates since the registers were last renormalised
+  int nu_ = 0;    // forward: orthogonal real 2x2 ops applied in unit-row form (their g's scale the store)
 
   int nthreads() const { return 1 << (k_ - r_); }
   void flush_pending(bool all);
@@ -606,6 +608,24 @@ bool SegGen::emit_op(const TOp& t) {
           if (!((e >> m) & 1) && qual(e)) std::swap(vm_[e], vm_[e | (1 << m)]);
         return true;
       }
+      if (t.kind == K_DENSE1R && !adj_ && (t.special == 1 || t.special == 2)) {
+        // g times a matrix with a unit entry per row; the form (pivot m00 or
+        // m10) is a launch-time bit, so angles do not change the kernel
+        if (!p.empty() || regc) return fail("internal: controlled op marked orthogonal");
+        const int j = nu_++;
+        const int sg = t.special == 1 ? 1 : -1;
+        o_ << "    if ((P.usel[" << (j >> 5) << "] >> " << (j & 31) << ") & 1u) {\n";
+        for (int form = 1; form >= 0; --form) {
+          if (form == 0) o_ << "    } else {\n";
+          for (int e = 0; e < R_; ++e) {
+            if ((e >> m) & 1) continue;
+            o_ << "      lqs::jit::" << (form ? "u1b" : "u1a") << "<A, " << sg << ">(" << V(e) << ", "
+               << V(e | (1 << m)) << ", " << cref(c) << ", " << cref(c + 1) << ");\n";
+          }
+        }
+        o_ << "    }\n";
+        return true;
+      }
       if (!p.empty()) o_ << "    if (" << p << ") {\n";
       each([&]() {
         for (int e = 0; e < R_; ++e) {
@@ -915,6 +935,11 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     }
   }
   flush_pending(true);
+  if (nu_) {
+    o_ << "    // the product of the unit-row forms' factors\n";
+    for (int e = 0; e < R_; ++e)
+      o_ << "    " << V(e) << " = lqs::jit::Lz<A>::rscale(lqs::jit::Re<A>::get(P.gscale), " << V(e) << ");\n";
+  }
   emit_store();  // natural order, or a layout that keeps sectors on lanes
   const std::string body = o_.str();
   const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^
@@ -930,7 +955,9 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
        "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n"
     << "#include \"tile.cuh\"\n#include \"jit_dev.cuh\"\n"
     << "typedef " << aname_ << " A;\n"
-    << "struct SegArgs {\n  lqs::TileGeom g;\n  A::C coef[" << std::max(ncoef, 1) << "];\n};\n";
+    << "struct SegArgs {\n  lqs::TileGeom g;\n  A::C coef[" << std::max(ncoef, 1) << "];\n";
+  if (nu_) s << "  A::C gscale;\n  uint32_t usel[" << (nu_ + 31) / 32 << "];\n";
+  s << "};\n";
   std::string head = replace_all(kSkeletonHead, "@NAME@", kname);
   head = replace_all(head, "@NTH@", std::to_string(nth));
   // resident CTAs per SM the register budget aims at: forward 2 x 256
@@ -1347,15 +1374,57 @@ static int entry_function(Entry* e, int dev, size_t smem, int threads, CUfunctio
   return LQS_OK;
 }
 
-// Kernel parameter block: the tile geometry, then the used coefficients.
+template <class A> struct CoefRe;
+template <> struct CoefRe<ArF32> { static double get(const float2& c) { return c.x; } };
+template <> struct CoefRe<ArF64> { static double get(const double2& c) { return c.x; } };
+template <> struct CoefRe<ArDF> { static double get(const DFK& c) { return (double)c.re.h + (double)c.re.l; } };
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Kernel parameter block: the tile geometry, then the used coefficients.  A
+// forward program passes its orthogonal real 2x2 ops (special 1, 2) in
+// unit-row form (jit_dev.cuh u1a / u1b): k0, k1 in the op's first two
+// coefficients, then the product of their factors g and one form bit per op,
+// numbered in op order as the generator numbers them.
 template <class A>
-static std::vector<unsigned char> seg_args(const TileProg<A>& P) {
+static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
   using C = typename A::C;
-  const size_t off = (sizeof(TileGeom) + alignof(C) - 1) / alignof(C) * alignof(C);
+  std::vector<C> coef(P.coef, P.coef + P.ncoef);
+  std::vector<uint32_t> usel;
+  double gprod = 1.0;
+  int nu = 0;
+  for (int i = 0; forward && i < P.nops; ++i) {
+    const TOp& t = P.op[i];
+    if (t.kind != K_DENSE1R || (t.special != 1 && t.special != 2)) continue;
+    const double m00 = CoefRe<A>::get(coef[t.coef]), m01 = CoefRe<A>::get(coef[t.coef + 1]);
+    const double m10 = CoefRe<A>::get(coef[t.coef + 2]), m11 = CoefRe<A>::get(coef[t.coef + 3]);
+    const bool form_b = std::fabs(m01) > std::fabs(m00);
+    const double g = form_b ? m10 : m00;
+    double k0 = 0.0, k1 = 0.0;
+    if (g != 0.0) {
+      k0 = (form_b ? m00 : m01) / g;
+      k1 = (form_b ? m11 : m10) / g;
+    }
+    coef[t.coef] = A::cconst(k0, 0.0);
+    coef[t.coef + 1] = A::cconst(k1, 0.0);
+    gprod *= g;
+    if ((size_t)(nu >> 5) >= usel.size()) usel.push_back(0u);
+    if (form_b) usel[nu >> 5] |= 1u << (nu & 31);
+    ++nu;
+  }
+  const size_t off = round_up(sizeof(TileGeom), alignof(C));
   const size_t nc = (size_t)std::max(P.ncoef, 1);
-  std::vector<unsigned char> args((off + nc * sizeof(C) + 15) / 16 * 16, 0);
+  const size_t goff = off + nc * sizeof(C);
+  const size_t uoff = round_up(goff + sizeof(C), alignof(uint32_t));
+  const size_t end = nu ? uoff + usel.size() * sizeof(uint32_t) : goff;
+  std::vector<unsigned char> args(round_up(end, 16), 0);
   std::memcpy(args.data(), &P.g, sizeof(TileGeom));
-  std::memcpy(args.data() + off, P.coef, (size_t)P.ncoef * sizeof(C));
+  if (P.ncoef) std::memcpy(args.data() + off, coef.data(), (size_t)P.ncoef * sizeof(C));
+  if (nu) {
+    const C gc = A::cconst(gprod, 0.0);
+    std::memcpy(args.data() + goff, &gc, sizeof(C));
+    std::memcpy(args.data() + uoff, usel.data(), usel.size() * sizeof(uint32_t));
+  }
   return args;
 }
 
@@ -1373,7 +1442,7 @@ int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, 
   CUfunction fn;
   int per_sm;
   LQS_TRY(entry_function(e, dev, smem, threads, &fn, &per_sm));
-  std::vector<unsigned char> args = seg_args(P);
+  std::vector<unsigned char> args = seg_args(P, true);
   void* psi = sv->d;
   int* status = sv->d_status;
   void* kp[] = {&psi, args.data(), &status};
@@ -1423,7 +1492,7 @@ int jit_launch_adjoint(void* entry, const TileProg<A>& P, int r, SV* sv, void* l
   CUfunction fn;
   int per_sm;
   LQS_TRY(entry_function(e, dev, smem, threads, &fn, &per_sm));
-  std::vector<unsigned char> args = seg_args(P);
+  std::vector<unsigned char> args = seg_args(P, false);
   void* psi = sv->d;
   int* status = sv->d_status;
   void* kp[] = {&psi, &lam, args.data(), &partial, &status};

@@ -35,6 +35,20 @@ template <class A> struct Lz {
   }
   static __device__ __forceinline__ C kmul(const C& a, const C& b) { return A::kmul(a, b); }
   static __device__ __forceinline__ void renorm(W&) {}
+  // SX x + k y for a real k
+  template <int SX>
+  static __device__ __forceinline__ W uma(const W& x, const R& k, const W& y) {
+    W r;
+    r.x = k * y.x + (SX > 0 ? x.x : -x.x);
+    r.y = k * y.y + (SX > 0 ? x.y : -x.y);
+    return r;
+  }
+  static __device__ __forceinline__ W rscale(const R& g, const W& x) {
+    W r;
+    r.x = g * x.x;
+    r.y = g * x.y;
+    return r;
+  }
 };
 template <> struct Lz<ArDF> {
   using W = DFC;
@@ -87,6 +101,23 @@ template <> struct Lz<ArDF> {
     w.re = df_norm(DAcc{w.re.h, w.re.l});
     w.im = df_norm(DAcc{w.im.h, w.im.l});
   }
+  // SX x + k y for a real k: one exact product, one TwoSum and the error terms
+  template <int SX>
+  static __device__ __forceinline__ DF uma1(const DF& x, const DF& k, const DF& y) {
+    const DAcc q = df_prod(y, k);
+    const float xh = SX > 0 ? x.h : -x.h, xl = SX > 0 ? x.l : -x.l;
+    const float s = fadd(q.s, xh);
+    const float bp = fsub(s, q.s);
+    const float err = fadd(fsub(q.s, fsub(s, bp)), fsub(xh, bp));
+    return DF{s, fadd(q.e, fadd(err, xl))};
+  }
+  template <int SX>
+  static __device__ __forceinline__ W uma(const W& x, const DF& k, const W& y) {
+    return W{uma1<SX>(x.re, k, y.re), uma1<SX>(x.im, k, y.im)};
+  }
+  static __device__ __forceinline__ W rscale(const DF& g, const W& x) {
+    return W{raw(df_prod(x.re, g)), raw(df_prod(x.im, g))};
+  }
 };
 
 template <class A>
@@ -113,6 +144,29 @@ __device__ __forceinline__ void d1r(typename A::W& a, typename A::W& b, const ty
   const typename A::W x = a, y = b;
   a = Lz<A>::rmac2(Re<A>::get(u00), x, Re<A>::get(u01), y);
   b = Lz<A>::rmac2(Re<A>::get(u10), x, Re<A>::get(u11), y);
+}
+
+// A real 2x2 that is g times an orthogonal matrix, m11 = SG m00 and
+// m10 = -SG m01 with SG = +-1 (rotations such as RY, reflections such as H).
+// Divided by m00 or m10, whichever has the larger modulus, each row keeps one
+// entry of modulus 1, so each output costs one product and one sum:
+//   form A (g = m00, |m00| >= |m01|): a' = a + k0 b,     b' = SG b + k1 a
+//   form B (g = m10, |m01| >  |m00|): a' = -SG b + k0 a,  b' = a + k1 b
+// with |k0|, |k1| <= 1 for orthogonal matrices.  The caller multiplies the
+// amplitudes by the product of the g's afterwards (rscale).
+template <class A, int SG>
+__device__ __forceinline__ void u1a(typename A::W& a, typename A::W& b, const typename A::C& k0,
+                                    const typename A::C& k1) {
+  const typename A::W x = a, y = b;
+  a = Lz<A>::template uma<1>(x, Re<A>::get(k0), y);
+  b = Lz<A>::template uma<SG>(y, Re<A>::get(k1), x);
+}
+template <class A, int SG>
+__device__ __forceinline__ void u1b(typename A::W& a, typename A::W& b, const typename A::C& k0,
+                                    const typename A::C& k1) {
+  const typename A::W x = a, y = b;
+  a = Lz<A>::template uma<-SG>(y, Re<A>::get(k0), x);
+  b = Lz<A>::template uma<1>(x, Re<A>::get(k1), y);
 }
 
 // (x0..x3) <- U x with U row-major at u[0..15]

@@ -263,3 +263,32 @@ def test_autotune_choice_is_used_and_correct(jit_on):
     assert err <= TOL["c128"]
     n_seg = L.lqs_plan_fused(n, "c128", c.ops, best)[0]
     assert n_seg >= 1
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_orthogonal_2x2_forms_at_edge_angles(jit_on, dtype, arith):
+    """Uncontrolled RY and H run in compiled segments as g times a matrix
+    with a unit entry per row, pivoting on m00 or m10 by which is larger.
+    Angles on both sides of the switch, at the tie |cos| = |sin|, at the
+    zeros of each entry and beyond 2 pi; reflections and a rotation given as
+    matrices; targets on register slots, thread bits and outside the tile."""
+    L, before = jit_on
+    set_mode(arith)
+    n = 14
+    angles = [0.0, np.pi, -np.pi, np.pi / 2, -np.pi / 2, 1.2, 2.0, -2.9, 3 * np.pi, 7.0, 1e-9, np.pi - 1e-9]
+    c = W.Circuit(n)
+    for i, th in enumerate(angles * 2):
+        q = (3 * i) % n
+        c.add("RY", (q,), (th,))
+        if i % 3 == 0:
+            c.add("H", ((q + 5) % n,))
+    for th in (0.3, 2.5, np.pi):
+        co, si = np.cos(th / 2), np.sin(th / 2)
+        c.add("U2", (int(th * 4) % n,), matrix=np.array([[co, si], [si, -co]], dtype=np.complex128))
+    c.add("U2", (9,), matrix=np.array([[0.6, -0.8], [0.8, 0.6]], dtype=np.complex128))
+    psi0 = W.gaussian_state(n, 404)
+    with gpu_state(n, dtype, psi0) as sv:
+        sv.apply(c, fused=True)
+        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
+    assert err <= TOL[dtype], err
+    assert L.lqs_jit_info()["launches"] > before["launches"]
