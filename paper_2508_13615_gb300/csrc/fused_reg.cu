@@ -34,7 +34,7 @@ namespace lqs {
 template <class A> int add_tile_op(TileProg<A>& P, const KOp& o, int gslot);
 template <class A> void init_prog(TileProg<A>& P, int n, uint64_t Q, int k, int b);
 
-constexpr int kRegThreadBits = 8;
+constexpr int kRegThreadBits = 9;
 constexpr int kMaxGradSlotsReg = 128;  // gradient slots per compiled adjoint segment
 constexpr int kRegThreads = 1 << kRegThreadBits;
 

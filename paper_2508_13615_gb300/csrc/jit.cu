@@ -58,6 +58,19 @@ uint32_t host_swz(uint32_t j, int sz) {
   return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
 }
 
+// An exchange's swizzle: swz<sz> with the bank bits of some positions
+// changed.  dm[b] lists the positions whose contribution to bank bit b
+// flips (jit_dev.cuh pfold); all zero is swz<sz> itself.
+struct XSwz {
+  uint32_t dm[4] = {0, 0, 0, 0};
+  bool plain() const { return !(dm[0] | dm[1] | dm[2] | dm[3]); }
+};
+uint32_t host_xswz(uint32_t j, int sz, const XSwz& x) {
+  uint32_t f = 0;
+  for (int b = 0; b < 4; ++b) f |= (uint32_t)(__builtin_popcount(j & x.dm[b]) & 1) << b;
+  return host_swz(j, sz) ^ f;
+}
+
 constexpr int kMaxGradSlotsJit = 128;  // gradient slots per compiled adjoint segment
 // Amplitude updates between renormalisations of the double-float registers.
 // The updates leave their results unrenormalised (jit_dev.cuh), and the low
@@ -147,6 +160,8 @@ class SegGen {
   std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
   std::string barrier_for(uint64_t to);
   bool emit_op(const TOp& t);
+  XSwz pick_swizzle(const int* wpos, const int* rpos) const;
+  std::string swz_expr(const std::string& j, const XSwz& x) const;
   bool emit_grad(const TOp& t);
   bool emit_grad_block(const TOp* ops, int count);
   void emit_layout(const TOp& t);
@@ -237,6 +252,67 @@ std::string SegGen::barrier_for(uint64_t to) {
   return bar;
 }
 
+// A warp's shared-memory access is served 128 bytes at a time, so the lanes
+// of one phase (lane bits 0..nb-1: 8 lanes of 16-byte amplitudes, 16 of
+// 8-byte ones) conflict unless their addresses fall in distinct bank groups.
+// The bank group of a swizzled position is a linear map F of its bits (the
+// low nb bits, plus the folded higher ones).  An exchange is conflict-free on
+// both sides when F is one-to-one on the lane positions of the layout that
+// writes and on those of the layout that reads.  The default fold of
+// positions mod nb fails when two lane positions share a residue, so each
+// exchange re-assigns the fold of the higher lane positions when it must
+// (a small backtracking search), writes and reads through that swizzle, and
+// leaves every other exchange on the default.
+XSwz SegGen::pick_swizzle(const int* wpos, const int* rpos) const {
+  const int nb = sz_ == 16 ? 3 : 4;
+  XSwz x;
+  if (k_ - r_ < nb) return x;
+  auto dflt = [&](int p) { return host_swz(1u << p, sz_) & ((1u << nb) - 1u); };  // bank bits of swz<sz>
+  uint32_t g[16];
+  for (int p = 0; p < 16; ++p) g[p] = dflt(p);
+  auto full_rank = [&](const int* pos) {
+    uint32_t span = 1u;  // bit v set: vector v is in the span
+    for (int i = 0; i < nb; ++i) {
+      const uint32_t v = g[pos[i]];
+      uint32_t next = span;
+      for (uint32_t u = 0; u < (1u << nb); ++u)
+        if ((span >> u) & 1u) next |= 1u << (u ^ v);
+      span = next;
+    }
+    return span == (nb == 3 ? 0xFFu : 0xFFFFu);
+  };
+  if (full_rank(wpos) && full_rank(rpos)) return x;
+  std::vector<int> free_pos;  // lane positions above the low bits: their fold can change
+  for (int i = 0; i < nb; ++i) {
+    for (int p : {wpos[i], rpos[i]})
+      if (p >= nb && std::find(free_pos.begin(), free_pos.end(), p) == free_pos.end()) free_pos.push_back(p);
+  }
+  std::function<bool(size_t)> search = [&](size_t i) {
+    if (i == free_pos.size()) return full_rank(wpos) && full_rank(rpos);
+    const int p = free_pos[i];
+    for (uint32_t v = 1; v < (1u << nb); ++v) {
+      g[p] = v;
+      if (search(i + 1)) return true;
+    }
+    g[p] = dflt(p);
+    return false;
+  };
+  if (!search(0)) return x;  // cannot happen for distinct positions; keep the default
+  for (int p = nb; p < k_; ++p) {
+    const uint32_t d = g[p] ^ dflt(p);
+    for (int b = 0; b < nb; ++b)
+      if ((d >> b) & 1u) x.dm[b] |= 1u << p;
+  }
+  return x;
+}
+
+std::string SegGen::swz_expr(const std::string& j, const XSwz& x) const {
+  std::string e = "lqs::jit::swz<" + std::to_string(sz_) + ">(" + j + ")";
+  if (x.plain()) return e;
+  return e + " ^ lqs::jit::pfold(" + j + ", " + hex32(x.dm[0]) + ", " + hex32(x.dm[1]) + ", " + hex32(x.dm[2]) +
+         ", " + hex32(x.dm[3]) + ")";
+}
+
 void SegGen::emit_layout(const TOp& t) {
   // Each state is written in the current layout and read back in the new one
   // through its own buffer.  The buffers alternate, so one barrier per state
@@ -248,10 +324,18 @@ void SegGen::emit_layout(const TOp& t) {
   const int saved_slot[4] = {slot_[0], slot_[1], slot_[2], slot_[3]};
   int saved_thr[16];
   std::copy(thr_, thr_ + 16, saved_thr);
+  // lane positions of the writing and the reading layout
+  int wpos[4], rpos[4];
+  for (int i = 0; i < 4; ++i) wpos[i] = i < k_ - r_ ? thr_[i] : 0;
+  for (int i = 0; i < 4; ++i) {
+    const int q = r_ + i < k_ ? (int)((t.ecmask >> (4 * (r_ + i))) & 15u) : 0;
+    rpos[i] = q;
+  }
+  const XSwz xs = pick_swizzle(wpos, rpos);
   std::string jo;
   if (adj_) {
     jo = fresh("jo");
-    o_ << "    const uint32_t " << jo << " = lqs::jit::swz<" << sz_ << ">(jt);\n";
+    o_ << "    const uint32_t " << jo << " = " << swz_expr("jt", xs) << ";\n";
   }
   bool first = true;
   each([&]() {
@@ -261,16 +345,16 @@ void SegGen::emit_layout(const TOp& t) {
     std::copy(saved_thr, saved_thr + 16, thr_);
     const std::string bar = barrier_for(t.ecmask);
     if (adj_) o_ << "    { const uint32_t sj = " << jo << ";\n";
-    else o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+    else o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
     for (int e = 0; e < R_; ++e)
-      o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_swz(old_je[e], sz_)) << "], " << V(e) << ");\n";
+      o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_xswz(old_je[e], sz_, xs)) << "], " << V(e) << ");\n";
     o_ << "    }\n    " << bar << "\n";
     set_layout(t.ecmask);  // validated by the caller
     if (first) o_ << "    jt = " << jt_expr() << ";\n";
     first = false;
-    o_ << "    { const uint32_t sj = lqs::jit::swz<" << sz_ << ">(jt);\n";
+    o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
     for (int e = 0; e < R_; ++e)
-      o_ << "      " << pfx_ << e << " = lqs::ld_w(&" << X << "[sj ^ " << hex32(host_swz(je(e), sz_)) << "]);\n";
+      o_ << "      " << pfx_ << e << " = lqs::ld_w(&" << X << "[sj ^ " << hex32(host_xswz(je(e), sz_, xs)) << "]);\n";
     o_ << "    }\n";
   });
   for (int e = 0; e < R_; ++e) vm_[e] = e;

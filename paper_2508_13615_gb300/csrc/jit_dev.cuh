@@ -208,6 +208,18 @@ __device__ __forceinline__ uint32_t swz(uint32_t j) {
   return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
 }
 
+// Bank bits an exchange's swizzle changes relative to swz: bit b is the
+// parity of the position bits in m_b (the masks are literal constants, so
+// unused ones vanish at compile time).
+__device__ __forceinline__ uint32_t pfold(uint32_t j, uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3) {
+  uint32_t f = 0;
+  if (m0) f |= (uint32_t)__popc(j & m0) & 1u;
+  if (m1) f |= ((uint32_t)__popc(j & m1) & 1u) << 1;
+  if (m2) f |= ((uint32_t)__popc(j & m2) & 1u) << 2;
+  if (m3) f |= ((uint32_t)__popc(j & m3) & 1u) << 3;
+  return f;
+}
+
 // Issues the bulk copies of one tile into `buf`, one row per thread (rows
 // beyond the block size wrap): the work is spread over the block instead of
 // one warp, so no warp falls behind the others before the next barrier.

@@ -7,7 +7,8 @@ Usage (for example under ``ncu -k regex:k_fused_reg``)::
 Cases: ``fused`` (2-layer RY/RZ/CNOT ansatz on the fused path, applied three
 times), ``qft`` (QFT on the fused path, three times), ``expval`` (TFIM
 expectation, three times), ``adjoint`` (adjoint gradient of a 2-layer
-ansatz), ``gate`` (one dense H per qubit on the plain path).  States start at
+ansatz), ``gate`` (one dense H per qubit on the plain path), ``u4`` (the
+Haar 4x4 gates of the single-gate sweep, U4(t, t+1), on the plain path).  States start at
 |0..0>; the sizes default to 24 qubits so the state (256 MiB complex128)
 exceeds the 129 MB L2 while a full ncu capture stays short.
 """
@@ -52,6 +53,10 @@ def main(argv=None) -> None:
     elif mode == "gate":
         for q in range(n):
             sv.apply_gate("H", (q,))
+    elif mode == "u4":
+        for _, c in W.sweep_30q(n):
+            if c.ops[0].name == "U4":
+                sv.apply(c, fused=False)
     else:
         raise SystemExit(f"unknown case {mode}")
     torch.cuda.synchronize()

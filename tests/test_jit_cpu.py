@@ -111,3 +111,68 @@ def test_adjoint_kernels_compile(dtype, arith):
     # a state that fits one adjoint tile compiles nothing
     c = W.ansatz(9, 2, 1)
     assert L.lqs_jit_precompile_adjoint(9, dtype, c.ops, c.params, arith) == 0
+
+
+def _bank_model(src):
+    """Extra shared-memory wavefronts of a generated kernel's exchanges, per
+    warp and tile: each 128-byte phase of a warp access costs one wavefront
+    per amplitude that shares a bank group with another lane's."""
+    import re
+
+    def swz(j, sz):
+        return j ^ ((((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7) if sz == 16 else (((j >> 4) ^ (j >> 8)) & 15))
+
+    def pfold(j, *m):
+        return sum((bin(j & mb).count("1") & 1) << b for b, mb in enumerate(m))
+
+    sz = 8 if "lqs::ArF32" in src else 16
+    per = 128 // sz
+    jt = sj = None
+    named = {}
+    extra = 0
+    for line in src.splitlines():
+        s = line.strip()
+        m = re.match(r"(?:uint32_t )?jt = (.*);$", s)
+        if m:
+            jt = m.group(1)
+        m = re.match(r"const uint32_t (jo\d+) = (.*);$", s)
+        if m:  # adjoint: one swizzled index for the writes of both states
+            named[m.group(1)] = m.group(2)
+            continue
+        m = re.match(r"\{ const uint32_t sj = (.*);$", s)
+        if m:
+            sj = named.get(m.group(1), m.group(1))
+            continue
+        if sj and ("st_w(&" in s or "ld_w(&" in s):
+            c = int(re.search(r"sj \^ (0x[0-9a-f]+)u", s).group(1), 16)
+            expr = re.sub(r"lqs::jit::swz<(\d+)>\(jt\)", r"swz(jt, \1)", sj).replace("lqs::jit::pfold", "pfold")
+            expr = re.sub(r"(0x[0-9a-f]+)u", r"\1", expr)
+            for ph in range(32 // per):
+                groups = {}
+                for lane in range(per * ph, per * (ph + 1)):
+                    j = eval(re.sub(r"(0x[0-9a-f]+)u", r"\1", jt).replace("u", ""), {"tid": lane})
+                    a = eval(expr, {"swz": swz, "pfold": pfold, "jt": j}) ^ c
+                    groups[a % per] = groups.get(a % per, 0) + 1
+                extra += max(groups.values()) - 1
+        elif sj and s.startswith("}"):
+            sj = None
+    return extra
+
+
+def test_exchanges_are_bank_conflict_free(tmp_path, monkeypatch):
+    """Every layout exchange of generated kernels (forward and adjoint, both
+    amplitude sizes) writes and reads shared memory without bank conflicts:
+    each exchange gets a swizzle that is one-to-one on the lane positions of
+    both the writing and the reading layout."""
+    import glob
+    monkeypatch.setenv("LQS_JIT_DUMP", str(tmp_path))
+    for dtype, arith in (("c128", L.LQS_ARITH_DF), ("c64", L.LQS_ARITH_AUTO)):
+        c = W.ansatz(24, 4, 3)
+        L.lqs_jit_precompile(24, dtype, c.ops, c.params, arith)
+        c = W.random_circuit(19, 120, seed=64)
+        L.lqs_jit_precompile(19, dtype, c.ops, c.params, arith)
+        L.lqs_jit_precompile_adjoint(19, dtype, c.ops, c.params, arith)
+    files = glob.glob(str(tmp_path / "*.cu"))
+    assert files
+    bad = {f: e for f in files for e in [_bank_model(open(f).read())] if e}
+    assert not bad, bad
