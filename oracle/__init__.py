@@ -108,8 +108,8 @@ def apply_matrix(psi: np.ndarray, n: int, wires: Sequence[int], U: np.ndarray) -
     """In place: psi <- U_full psi for U on ``wires``."""
     _check_state(psi, n)
     w = np.asarray(wires, dtype=np.int32)
-    if not 1 <= len(w) <= 4 or U.shape != (1 << len(w), 1 << len(w)):
-        raise ValueError("apply_matrix takes 1 to 4 wires and a matching square matrix")
+    if not 1 <= len(w) <= 7 or U.shape != (1 << len(w), 1 << len(w)):
+        raise ValueError("apply_matrix takes 1 to 7 wires and a matching square matrix")
     Uc = np.ascontiguousarray(U, dtype=np.complex128)
     lib().oracle_apply_matrix(_dp(psi.view(np.float64)), n, _ip(w), len(w), _dp(Uc.view(np.float64)))
     return psi

@@ -174,21 +174,23 @@ static uint64_t group_index(uint64_t base, const int* wires, int m, int a) {
  * psi <- U_full psi for the 2^m x 2^m matrix U (interleaved re,im, row-major)
  * acting on `wires`.  Every index whose wire bits are all zero is the base of
  * one group of 2^m amplitudes; the group is gathered, multiplied by U and
- * scattered back.  Wires must be distinct and < n; m <= 4.
+ * scattered back.  Wires must be distinct and < n; 1 <= m <= 7 (single gates
+ * have at most 4 wires; dense blocks up to 7).
  */
 void oracle_apply_matrix(double* psi_ri, int n, const int* wires, int m, const double* U_ri) {
   cplx* psi = (cplx*)psi_ri;
-  cplx U[256];
-  if (m < 1 || m > 4) return; /* the buffers hold at most 4 wires (the wrapper rejects more) */
+  if (m < 1 || m > 7) return; /* the group buffers hold at most 7 wires (the wrapper rejects more) */
   int dim = 1 << m;
+  cplx* U = (cplx*)malloc(sizeof(cplx) * (size_t)dim * (size_t)dim);
+  if (!U) return;
   uint64_t N = (uint64_t)1 << n, wmask = 0;
   for (int k = 0; k < dim * dim; ++k) U[k] = U_ri[2 * k] + I * U_ri[2 * k + 1];
   for (int k = 0; k < m; ++k) wmask |= (uint64_t)1 << wires[k];
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < (int64_t)N; ++i) {
     if ((uint64_t)i & wmask) continue;
-    cplx v[16], r[16];
-    uint64_t idx[16];
+    cplx v[128], r[128];
+    uint64_t idx[128];
     for (int a = 0; a < dim; ++a) {
       idx[a] = group_index((uint64_t)i, wires, m, a);
       v[a] = psi[idx[a]];
@@ -200,6 +202,7 @@ void oracle_apply_matrix(double* psi_ri, int n, const int* wires, int m, const d
     }
     for (int a = 0; a < dim; ++a) psi[idx[a]] = r[a];
   }
+  free(U);
 }
 
 /*

@@ -473,3 +473,30 @@ def test_double_excitation_four_term_shift_matches_finite_differences():
         p[k] -= 2 * h
         em = oracle.energy(c, terms, p)
         assert abs((ep - em) / (2 * h) - g[k]) < 1e-8
+
+
+@pytest.mark.parametrize("m,wires", [(5, (0, 1, 2, 3, 4)), (5, (4, 3, 2, 1, 0)), (6, (7, 2, 5, 0, 3, 6)),
+                                     (7, (1, 0, 7, 6, 3, 5, 2))])
+def test_dense_blocks_match_tensor_contraction(m, wires):
+    """The general update with 5 to 7 wires (dense blocks) equals the full
+    operator built by numpy tensor contraction, for a Haar matrix on ordered
+    and scrambled wires."""
+    n = 8
+    U = W.haar_unitary(1 << m, 77, m)
+    psi = rand_state(n, 33 + m)
+    want = full_operator(n, wires, U) @ psi
+    got = oracle.apply_matrix(psi.copy(), n, wires, U)
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_dense_block_of_a_product_is_the_product():
+    """A 6-wire block that is the Kronecker product of two 3-wire matrices
+    equals applying the two factors one after the other (first listed wires
+    most significant)."""
+    n = 9
+    Ua, Ub = W.haar_unitary(8, 78, 1), W.haar_unitary(8, 78, 2)
+    wires = (8, 1, 4, 0, 6, 3)
+    psi = rand_state(n, 40)
+    got = oracle.apply_matrix(psi.copy(), n, wires, np.kron(Ua, Ub))
+    want = oracle.apply_matrix(oracle.apply_matrix(psi.copy(), n, wires[3:], Ub), n, wires[:3], Ua)
+    assert np.max(np.abs(got - want)) < 1e-13
