@@ -538,6 +538,81 @@ def config_sweep30(args):
     print(json.dumps({"config": "sweep30", "n_qubits": n, "state_bytes": S, "rows": rows}), flush=True)
 
 
+def config_tcblock30(args):
+    """Dense 32x32 blocks on the tensor cores at 30 qubits complex64: one
+    block pass (tcgen05 3xTF32) against the same run of gates on the fused
+    path (40 Haar U4 gates on neighbouring pairs of qubits 0..4, compiled
+    segments), with the block's matrix formed on the host from the gates."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    n = args.n
+    pk = peaks()
+    L.lqs_set_jit(L.LQS_JIT_ON)
+    sv = L.StateVector(n, "c64")
+    st = torch.cuda.current_stream()
+    c = W.Circuit(n)
+    U = np.eye(32, dtype=np.complex128)
+    for g in range(40):
+        q = (g * 3) % 4  # pairs (q, q + 1) inside qubits 0..4
+        M = W.haar_unitary(4, 61, g)
+        c.add("U4", (q + 1, q), matrix=M)
+        # M acts on (qubit q+1, qubit q) as (most, least) significant local bits
+        T = M.reshape(2, 2, 2, 2)
+        op = np.zeros((32, 32), dtype=np.complex128)
+        for k in range(32):
+            e = np.zeros(32, dtype=np.complex128)
+            e[k] = 1
+            t = e.reshape(2, 2, 2, 2, 2)  # axes: qubit 4, 3, 2, 1, 0
+            ax = (4 - (q + 1), 4 - q)
+            r = np.tensordot(T, t, axes=([2, 3], list(ax)))
+            r = np.moveaxis(r, [0, 1], list(ax))
+            op[:, k] = r.reshape(32)
+        U = op @ U
+    L.lqs_jit_precompile(n, "c64", c.ops, c.params, L.LQS_ARITH_AUTO)
+
+    def t_of(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = _events()
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    L.lqs_sv_set_basis(sv.h, 0)
+    L.lqs_apply_fused(sv.h, L.OpArray([W.Op("H", (q,)) for q in range(n)]), np.zeros(1), None)
+    ref = sv.tensor.clone()
+    ms_block = t_of(lambda: L.lqs_apply_block(sv.h, 5, U))
+    ops = L.OpArray(c.ops)
+    ms_fused = t_of(lambda: L.lqs_apply_fused(sv.h, ops, c.params, None))
+    # one application each from the same input, compared
+    sv.tensor.copy_(ref)
+    L.lqs_apply_block(sv.h, 5, U)
+    a = sv.tensor.clone()
+    sv.tensor.copy_(ref)
+    L.lqs_apply_fused(sv.h, ops, c.params, None)
+    diff = float((a - sv.tensor).abs().max().item())
+    scale = float(sv.tensor.abs().max().item())
+    S = (1 << n) * 8
+    gbs = 2 * S / (ms_block * 1e-3) / 1e9
+    flops = ((1 << n) // 32) * 64 * 64 * 2 * 3  # per row of 32 amplitudes: a 64 x 64 real product, three times
+    print(json.dumps({
+        "config": "tcblock30", "n_qubits": n, "dtype": "c64", "state_bytes": S,
+        "block": "32x32 complex on qubits 0..4, tcgen05.mma kind::tf32, 3xTF32",
+        "block_ms": ms_block, "block_gbs": gbs,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / pk["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"},
+        "tensor_tflops": flops / (ms_block * 1e-3) / 1e12,
+        "fused_gates": len(c.ops), "fused_ms": ms_fused,
+        "speedup_vs_fused": ms_fused / ms_block,
+        "max_abs_diff_block_vs_fused": diff, "max_abs_amplitude": scale}), flush=True)
+    sv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,7 +622,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", default="main", choices=["main", "adjoint24", "precision32", "batch256", "sweep30"],
+    ap.add_argument("--config", default="main",
+                    choices=["main", "adjoint24", "precision32", "batch256", "sweep30", "tcblock30"],
                     help="secondary measurements (one JSON line each); the default is the headline run")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -559,7 +635,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         {"adjoint24": config_adjoint24, "precision32": config_precision32, "batch256": config_batch256,
-         "sweep30": config_sweep30}[args.config](args)
+         "sweep30": config_sweep30, "tcblock30": config_tcblock30}[args.config](args)
         return
 
     import torch

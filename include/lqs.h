@@ -181,6 +181,19 @@ LQS_API int lqs_apply_gate(lqs_sv* sv, int gate, const int* wires, int n_wires, 
  * dense kernels and no inspection of its structure. */
 LQS_API int lqs_apply_matrix(lqs_sv* sv, const int* wires, int n_wires, const double* matrix);
 
+/* Dense block on the tensor cores: the general approach of Sec. 3.1 applied
+ * to a set of qubits.  psi <- U psi for a 2^m x 2^m complex matrix U acting on
+ * qubits 0..m-1: U[j][k] maps the amplitude whose low m index bits read k to
+ * the one that reads j (qubit q is bit q of k).  `matrix` is row-major
+ * interleaved complex128 on the host (read during the call).
+ *
+ * Complex64 states only, m = 5, n >= m + 7 (LQS_ERR_UNSUPPORTED otherwise).
+ * The product runs as float32 matrix multiplies on the tensor cores with
+ * each operand split into a TF32 leading part and a residual (three
+ * products), about float32 accuracy; one pass over the state.  Asynchronous;
+ * a device-side timeout is reported by lqs_sv_sync (LQS_ERR_TIMEOUT). */
+LQS_API int lqs_apply_block(lqs_sv* sv, int m, const double* matrix);
+
 /* Fused path: the host planner groups the circuit into segments whose
  * non-diagonal targets fit one tile of 2^k amplitudes (low contiguous qubits
  * plus chosen high qubits); each segment is one HBM pass in which the tile is

@@ -128,6 +128,20 @@ def apply_op(psi: np.ndarray, n: int, op: Op, params: np.ndarray) -> np.ndarray:
     return apply_matrix(psi, n, op.wires, op_matrix(op, params))
 
 
+def apply_matrix_at(psi: np.ndarray, n: int, wires: Sequence[int], U: np.ndarray, indices: np.ndarray) -> np.ndarray:
+    """Amplitudes ``(U_full psi)[indices]`` for U on ``wires``, one by one (psi unchanged)."""
+    _check_state(psi, n)
+    w = np.asarray(wires, dtype=np.int32)
+    if not 1 <= len(w) <= 7 or U.shape != (1 << len(w), 1 << len(w)):
+        raise ValueError("apply_matrix_at takes 1 to 7 wires and a matching square matrix")
+    Uc = np.ascontiguousarray(U, dtype=np.complex128)
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    out = np.zeros(len(idx), dtype=np.complex128)
+    lib().oracle_apply_matrix_at(_dp(psi.view(np.float64)), n, _ip(w), len(w), _dp(Uc.view(np.float64)),
+                                 _up(idx), len(idx), _dp(out.view(np.float64)))
+    return out
+
+
 def apply_op_at(psi: np.ndarray, n: int, op: Op, params: np.ndarray, indices: np.ndarray) -> np.ndarray:
     """Amplitudes ``(U_op psi)[indices]`` computed one by one (psi unchanged)."""
     _check_state(psi, n)

@@ -93,6 +93,7 @@ def _load():
         "lqs_sv_copy_from_host": (i32, [vp, vp]),
         "lqs_sv_copy_to_host": (i32, [vp, vp]),
         "lqs_sv_copy_to_host_async": (i32, [vp, vp]),
+        "lqs_apply_block": (i32, [vp, ctypes.c_int, vp]),
         "lqs_sv_sync": (i32, [vp]),
         "lqs_apply_gate": (i32, [vp, i32, ip, i32, dp, i32, i32]),
         "lqs_apply_matrix": (i32, [vp, ip, i32, dp]),
@@ -265,6 +266,14 @@ def lqs_sv_copy_to_host_async(h, host: np.ndarray) -> np.ndarray:
         raise ValueError("host buffer must be contiguous")
     _check(_L.lqs_sv_copy_to_host_async(h, host.ctypes.data))
     return host
+
+
+def lqs_apply_block(h, m: int, matrix) -> None:
+    """Dense 2^m x 2^m complex matrix on qubits 0..m-1 (tensor cores; complex64, m = 5)."""
+    U = np.ascontiguousarray(matrix, dtype=np.complex128)
+    if U.shape != (1 << m, 1 << m):
+        raise ValueError("matrix must be 2^m x 2^m")
+    _check(_L.lqs_apply_block(h, int(m), U.ctypes.data))
 
 
 def lqs_sv_sync(h) -> None:

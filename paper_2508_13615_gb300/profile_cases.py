@@ -8,7 +8,9 @@ Cases: ``fused`` (2-layer RY/RZ/CNOT ansatz on the fused path, applied three
 times), ``qft`` (QFT on the fused path, three times), ``expval`` (TFIM
 expectation, three times), ``adjoint`` (adjoint gradient of a 2-layer
 ansatz), ``gate`` (one dense H per qubit on the plain path), ``u4`` (the
-Haar 4x4 gates of the single-gate sweep, U4(t, t+1), on the plain path).  States start at
+Haar 4x4 gates of the single-gate sweep, U4(t, t+1), on the plain path),
+``block`` (a Haar 32x32 block on qubits 0..4 on the tensor cores, three
+times; complex64 only).  States start at
 |0..0>; the sizes default to 24 qubits so the state (256 MiB complex128)
 exceeds the 129 MB L2 while a full ncu capture stays short.
 """
@@ -53,6 +55,11 @@ def main(argv=None) -> None:
     elif mode == "gate":
         for q in range(n):
             sv.apply_gate("H", (q,))
+    elif mode == "block":
+        U = W.haar_unitary(32, 91, 0)
+        L.lqs_apply_gate(sv.h, "H", (0,))
+        for _ in range(3):
+            L.lqs_apply_block(sv.h, 5, U)
     elif mode == "u4":
         for _, c in W.sweep_30q(n):
             if c.ops[0].name == "U4":
