@@ -123,6 +123,11 @@ typedef struct {
   int32_t low_qubits;  /* b: contiguous low qubits always in a tile (coalescing), 0 = auto */
   int32_t arith;       /* lqs_arith, c128 only */
   int32_t max_ops;     /* cap on gates per fused segment, 0 = no cap beyond the program size */
+  int32_t tc_blocks;   /* complex64, n >= 12: a run of gates confined to qubits 0..4 whose dense weight
+                          (4 per two-qubit dense gate, 1 per one-qubit dense gate, 1/4 per other gate)
+                          reaches this value is applied as one 32x32 block on the tensor cores
+                          (lqs_apply_block); gates on other qubits that commute with the run move past
+                          it.  0 = default (16), negative = never. */
 } lqs_fuse_cfg;
 
 /* ---- state vectors ----------------------------------------------------------- */

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "arith.cuh"
@@ -184,6 +185,52 @@ __global__ void k_distance(const SA* __restrict__ a, const SB* __restrict__ b, u
     part[2 * blockIdx.x] = r0[0];
     part[2 * blockIdx.x + 1] = r1[0];
   }
+}
+
+// Dense-block extraction for the tensor cores.  Ops confined to qubits
+// 0..kBlockQubits-1 gather into a run; ops on other qubits only commute with
+// the run and are deferred past it; an op that touches both ends the run.  A
+// run whose dense weight reaches `threshold` is emitted as one block matrix,
+// otherwise its ops go back into the fused stream (before the deferred ones,
+// which commute with them).  emit(ops, U): U is the block matrix, or null
+// for ops of the fused stream.
+template <class Emit>
+static void split_blocks(const std::vector<KOp>& kops, double threshold, Emit&& emit) {
+  const uint64_t win = (1ull << kBlockQubits) - 1;
+  std::vector<int> run, deferred;
+  double weight = 0.0;
+  auto flush = [&]() {
+    if (!run.empty() && weight >= threshold) {
+      double U[2 << (2 * kBlockQubits)];
+      block_matrix(kops, run, U);
+      emit(std::vector<KOp>(), U);
+    } else if (!run.empty()) {
+      std::vector<KOp> v;
+      for (int i : run) v.push_back(kops[i]);
+      emit(std::move(v), nullptr);
+    }
+    if (!deferred.empty()) {
+      std::vector<KOp> v;
+      for (int i : deferred) v.push_back(kops[i]);
+      emit(std::move(v), nullptr);
+    }
+    run.clear();
+    deferred.clear();
+    weight = 0.0;
+  };
+  for (int i = 0; i < (int)kops.size(); ++i) {
+    const uint64_t w = kops[i].wire_mask();
+    if (!(w & ~win)) {
+      run.push_back(i);
+      weight += block_weight(kops[i]);
+    } else if (!(w & win)) {
+      deferred.push_back(i);
+    } else {
+      flush();
+      emit(std::vector<KOp>{kops[i]}, nullptr);
+    }
+  }
+  flush();
 }
 
 }  // namespace lqs
@@ -427,15 +474,44 @@ int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* param
   PlanCfg pc;
   int arith = LQS_ARITH_AUTO;
   LQS_TRY(resolve_cfg(sv->n, sv->dtype, cfg, pc, &arith));
-  std::vector<Segment> segs;
-  LQS_TRY(plan_segments(sv->n, kops, pc, segs));
+  // Pieces in execution order: fused runs of lowered ops, and dense blocks
+  // on qubits 0..4 for the tensor cores (complex64).
+  struct Piece {
+    std::vector<KOp> ops;
+    std::vector<Segment> segs;
+    bool block = false;
+    double U[2 << (2 * kBlockQubits)];
+  };
+  std::vector<std::unique_ptr<Piece>> pieces;
+  const double tc_weight = !cfg || cfg->tc_blocks == 0 ? 16.0 : (double)cfg->tc_blocks;
+  if (sv->dtype == LQS_C64 && sv->n >= kBlockQubits + 7 && tc_weight > 0) {
+    split_blocks(kops, tc_weight, [&](std::vector<KOp>&& run, const double* U) {
+      if (U) {
+        pieces.emplace_back(new Piece());
+        pieces.back()->block = true;
+        std::memcpy(pieces.back()->U, U, sizeof(pieces.back()->U));
+      } else {
+        if (pieces.empty() || pieces.back()->block) pieces.emplace_back(new Piece());
+        for (KOp& k : run) pieces.back()->ops.push_back(k);
+      }
+    });
+  } else {
+    pieces.emplace_back(new Piece());
+    pieces.back()->ops = std::move(kops);
+  }
+  for (auto& p : pieces)
+    if (!p->block) LQS_TRY(plan_segments(sv->n, p->ops, pc, p->segs));
   if (jit_enabled_for(sv->n)) {  // compile the structures this call needs, in parallel, before launching
     std::vector<void*> todo;
-    for (const Segment& s : segs) LQS_TRY(jit_collect(sv->n, sv->dtype, arith, kops, s, pc, false, todo));
+    for (auto& p : pieces)
+      for (const Segment& s : p->segs) LQS_TRY(jit_collect(sv->n, sv->dtype, arith, p->ops, s, pc, false, todo));
     const int rc = jit_compile(todo);
     if (rc != LQS_OK && jit_mode() == LQS_JIT_ON) return rc;
   }
-  for (const Segment& s : segs) LQS_TRY(launch_segment(sv, kops, s, pc, arith));
+  for (auto& p : pieces) {
+    if (p->block) LQS_TRY(apply_block(sv, p->U));
+    for (const Segment& s : p->segs) LQS_TRY(launch_segment(sv, p->ops, s, pc, arith));
+  }
   return LQS_OK;
 }
 

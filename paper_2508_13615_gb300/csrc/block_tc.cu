@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -307,20 +308,104 @@ float tf32_round_host(float x) {
 }
 
 }  // namespace
-}  // namespace lqs
 
-using namespace lqs;
+// One lowered op applied to a register of kBlockQubits qubits (host, complex
+// double): the semantics of each kernel op kind (lqs_internal.cuh) on the 32
+// amplitudes, controls included.
+static void kop_apply_small(const KOp& o, std::complex<double>* v) {
+  using Z = std::complex<double>;
+  const int N = 1 << kBlockQubits;
+  const uint64_t cm = o.cmask;
+  auto coef = [&](int i) { return Z(o.m[2 * i], o.m[2 * i + 1]); };
+  auto on = [&](int i) { return ((uint64_t)i & cm) == cm; };
+  const int T0 = o.t0 >= 0 ? 1 << o.t0 : 0, T1 = o.t1 >= 0 ? 1 << o.t1 : 0;
+  switch (o.kind) {
+    case K_PHASE: {
+      const Z f = o.special == 1 ? Z(-1, 0) : o.special == 2 ? Z(0, 1) : o.special == 3 ? Z(0, -1) : coef(0);
+      for (int i = 0; i < N; ++i)
+        if (on(i)) v[i] *= f;
+      break;
+    }
+    case K_DIAG1:
+      for (int i = 0; i < N; ++i)
+        if (on(i)) v[i] *= coef((i & T0) ? 1 : 0);
+      break;
+    case K_DIAG2:
+      for (int i = 0; i < N; ++i)
+        if (on(i)) v[i] *= coef(2 * ((i & T0) ? 1 : 0) + ((i & T1) ? 1 : 0));
+      break;
+    case K_ANTI1:
+      for (int i = 0; i < N; ++i) {
+        if ((i & T0) || !on(i)) continue;
+        const Z a = v[i], b = v[i | T0];
+        if (o.special == 1) {
+          v[i] = b;
+          v[i | T0] = a;
+        } else {
+          v[i] = coef(0) * b;
+          v[i | T0] = coef(1) * a;
+        }
+      }
+      break;
+    case K_SWAP:
+      for (int i = 0; i < N; ++i) {
+        if (!(i & T0) || (i & T1) || !on(i)) continue;
+        std::swap(v[i], v[i ^ T0 ^ T1]);
+      }
+      break;
+    case K_DENSE1:
+    case K_DENSE1R:
+      for (int i = 0; i < N; ++i) {
+        if ((i & T0) || !on(i)) continue;
+        const Z a = v[i], b = v[i | T0];
+        Z u[4];
+        for (int k = 0; k < 4; ++k) u[k] = o.kind == K_DENSE1 ? coef(k) : Z(o.m[k], 0.0);
+        v[i] = u[0] * a + u[1] * b;
+        v[i | T0] = u[2] * a + u[3] * b;
+      }
+      break;
+    case K_DENSE2:
+      for (int i = 0; i < N; ++i) {
+        if ((i & T0) || (i & T1) || !on(i)) continue;
+        const int id[4] = {i, i | T1, i | T0, i | T0 | T1};  // local index 2 bit(t0) + bit(t1)
+        Z x[4], y[4];
+        for (int r = 0; r < 4; ++r) x[r] = v[id[r]];
+        for (int r = 0; r < 4; ++r) {
+          y[r] = 0;
+          for (int c = 0; c < 4; ++c) y[r] += coef(4 * r + c) * x[c];
+        }
+        for (int r = 0; r < 4; ++r) v[id[r]] = y[r];
+      }
+      break;
+    default:
+      break;
+  }
+}
 
-extern "C" int lqs_apply_block(lqs_sv* h, int m, const double* matrix) {
-  if (!h) return set_error(LQS_ERR_ARG, "sv is NULL");
-  if (!matrix) return set_error(LQS_ERR_ARG, "matrix is NULL");
-  SV* sv = reinterpret_cast<SV*>(h);
-  if (sv->dtype != LQS_C64) return set_error(LQS_ERR_UNSUPPORTED, "tensor-core blocks take complex64 states");
-  if (m != 5) return set_error(LQS_ERR_UNSUPPORTED, "tensor-core blocks have m = 5 qubits");
-  if (sv->n < m + 7) return set_error(LQS_ERR_UNSUPPORTED, "tensor-core blocks need at least m + 7 qubits");
-  const int dim = 1 << m;
-  for (int i = 0; i < 2 * dim * dim; ++i)
-    if (!std::isfinite(matrix[i])) return set_error(LQS_ERR_ARG, "matrix has a non-finite entry");
+void block_matrix(const std::vector<KOp>& ops, const std::vector<int>& idx, double* U) {
+  const int N = 1 << kBlockQubits;
+  std::complex<double> col[1 << kBlockQubits];
+  for (int k = 0; k < N; ++k) {
+    for (int j = 0; j < N; ++j) col[j] = j == k ? 1.0 : 0.0;
+    for (int i : idx) kop_apply_small(ops[i], col);
+    for (int j = 0; j < N; ++j) {
+      U[2 * (j * N + k)] = col[j].real();
+      U[2 * (j * N + k) + 1] = col[j].imag();
+    }
+  }
+}
+
+double block_weight(const KOp& op) {
+  switch (op.kind) {
+    case K_DENSE2: return 4.0;
+    case K_DENSE1:
+    case K_DENSE1R: return 1.0;
+    default: return 0.25;
+  }
+}
+
+int apply_block(SV* sv, const double* matrix) {
+  const int m = kBlockQubits, dim = 1 << m;
   // W^T in N-major rows (row n = output float, K contiguous), leading parts in
   // rows 0..63 and residuals in rows 64..127
   std::vector<float> B((size_t)2 * kTK * kTK);
@@ -359,4 +444,23 @@ extern "C" int lqs_apply_block(lqs_sv* h, int m, const double* matrix) {
   count_launch();
   LQS_CUDA_TRY(cudaGetLastError());
   return LQS_OK;
+}
+
+}  // namespace lqs
+
+using namespace lqs;
+
+extern "C" int lqs_apply_block(lqs_sv* h, int m, const double* matrix) {
+  void* dptr = nullptr;
+  int n = 0, dtype = 0;
+  LQS_TRY(lqs_sv_info(h, &dptr, &n, &dtype));  // validates the handle
+  if (!matrix) return set_error(LQS_ERR_ARG, "matrix is NULL");
+  SV* sv = reinterpret_cast<SV*>(h);
+  if (sv->dtype != LQS_C64) return set_error(LQS_ERR_UNSUPPORTED, "tensor-core blocks take complex64 states");
+  if (m != kBlockQubits) return set_error(LQS_ERR_UNSUPPORTED, "tensor-core blocks have m = 5 qubits");
+  if (sv->n < m + 7) return set_error(LQS_ERR_UNSUPPORTED, "tensor-core blocks need at least m + 7 qubits");
+  const int dim = 1 << m;
+  for (int i = 0; i < 2 * dim * dim; ++i)
+    if (!std::isfinite(matrix[i])) return set_error(LQS_ERR_ARG, "matrix has a non-finite entry");
+  return apply_block(sv, matrix);
 }

@@ -118,6 +118,20 @@ class SegGen {
   std::vector<std::pair<std::string, int>> pend_;  // gradient partials awaiting a batched warp sum
   int ntab_ = 0;  // entries of the shared table of outside-qubit factor products
   int lz_ = 0;    // amplitude updates since the registers were last renormalised
+  // Exchanges since the last block-wide barrier, for the ordering check of
+  // a buffer's next writes (exchange_safe): per exchange its buffer, the warp
+  // writing and the warp reading each buffer position, and its barrier's
+  // groups (warps agreeing on the tid bits of gmask; 0 = the whole block).
+  struct XRec {
+    int buf;
+    bool writes;  // its writes are not yet ordered before everything (no block barrier after them)
+    std::vector<uint8_t> wown, rown;
+    uint32_t gmask;
+  };
+  std::vector<XRec> xhist_;
+  std::vector<uint8_t> owners(const XSwz& xs) const;
+  std::vector<char> reach(int v, size_t from) const;
+  bool exchange_safe(int buf, const std::vector<uint8_t>& wown) const;
   int nu_ = 0;    // forward: orthogonal real 2x2 ops applied in unit-row form (their g's scale the store)
 
   int nthreads() const { return 1 << (k_ - r_); }
@@ -158,7 +172,7 @@ class SegGen {
   // predicate of the op's thread-held and outside controls ("" when none),
   // and the register-slot mask its register-held controls require
   std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
-  std::string barrier_for(uint64_t to);
+  std::string barrier_for(uint64_t to, uint32_t* gmask);
   bool emit_op(const TOp& t);
   XSwz pick_swizzle(const int* wpos, const int* rpos) const;
   std::string swz_expr(const std::string& j, const XSwz& x) const;
@@ -226,7 +240,7 @@ std::string SegGen::pred(uint32_t lc, uint64_t ec, uint32_t& regc) const {
 // another group are still at an earlier one, and two barrier instances must
 // never share an id.  When the ids run out the block barrier is used; block
 // barriers (here and at the top of the tile loop) make all ids free again.
-std::string SegGen::barrier_for(uint64_t to) {
+std::string SegGen::barrier_for(uint64_t to, uint32_t* gmask) {
   uint32_t fixed = 0, moved = 0;
   for (int m = 5; m < k_ - r_; ++m) {
     const int q = (int)((to >> (4 * (r_ + m))) & 15u);
@@ -234,9 +248,11 @@ std::string SegGen::barrier_for(uint64_t to) {
     else moved |= 1u << m;
   }
   const int groups = 1 << __builtin_popcount(fixed);
+  *gmask = fixed;
   if (!moved) return "__syncwarp();";
   if (!fixed || next_bar_ + groups - 1 > 15) {
     next_bar_ = 1;  // every warp passes it after all earlier group barriers completed
+    *gmask = 0;
     return "__syncthreads();";
   }
   std::string id;
@@ -313,6 +329,63 @@ std::string SegGen::swz_expr(const std::string& j, const XSwz& x) const {
          ", " + hex32(x.dm[3]) + ")";
 }
 
+// Buffer position -> the warp that holds the amplitude there, in the current
+// layout under swizzle xs.
+std::vector<uint8_t> SegGen::owners(const XSwz& xs) const {
+  std::vector<uint8_t> own((size_t)1 << k_, 0);
+  const int nt = nthreads();
+  for (int tid = 0; tid < nt; ++tid) {
+    uint32_t jt = 0;
+    for (int m = 0; m < k_ - r_; ++m)
+      if ((tid >> m) & 1) jt |= 1u << thr_[m];
+    for (int e = 0; e < R_; ++e) own[host_xswz(jt | je(e), sz_, xs)] = (uint8_t)(tid >> 5);
+  }
+  return own;
+}
+
+// Warps whose execution after the last recorded barrier is ordered after
+// something warp v did before barrier xhist_[from] (every later barrier
+// passes the order on to the warps of the group it synchronises).
+std::vector<char> SegGen::reach(int v, size_t from) const {
+  const int nw = nthreads() / 32;
+  std::vector<char> in((size_t)nw, 0);
+  in[(size_t)v] = 1;
+  for (size_t m = from; m < xhist_.size(); ++m) {
+    const uint32_t g = xhist_[m].gmask;
+    std::vector<char> nx((size_t)nw, 0);
+    for (int u = 0; u < nw; ++u)
+      if (in[(size_t)u])
+        for (int x = 0; x < nw; ++x)
+          if ((((uint32_t)u << 5) & g) == (((uint32_t)x << 5) & g)) nx[(size_t)x] = 1;
+    in.swap(nx);
+  }
+  return in;
+}
+
+// Whether the writes of a new exchange into buffer `buf` (position -> writing
+// warp) are ordered after every earlier access of the same positions since
+// the last block-wide barrier: the earlier writes (before their exchange's
+// barrier) and reads (after it).  Group barriers order only the warps of a
+// group, so a warp may run an exchange or two ahead of another group.
+bool SegGen::exchange_safe(int buf, const std::vector<uint8_t>& wown) const {
+  const int nw = nthreads() / 32;
+  for (size_t j = 0; j < xhist_.size(); ++j) {
+    const XRec& h = xhist_[j];
+    if (h.buf != buf) continue;
+    std::vector<std::vector<char>> rw((size_t)nw), rr((size_t)nw);
+    for (int v = 0; v < nw; ++v) {
+      if (h.writes) rw[(size_t)v] = reach(v, j);
+      rr[(size_t)v] = reach(v, j + 1);
+    }
+    for (size_t p = 0; p < wown.size(); ++p) {
+      const int w = wown[p];
+      if (h.writes && !rw[h.wown[p]][(size_t)w]) return false;
+      if (!rr[h.rown[p]][(size_t)w]) return false;
+    }
+  }
+  return true;
+}
+
 void SegGen::emit_layout(const TOp& t) {
   // Each state is written in the current layout and read back in the new one
   // through its own buffer.  The buffers alternate, so one barrier per state
@@ -338,12 +411,29 @@ void SegGen::emit_layout(const TOp& t) {
     o_ << "    const uint32_t " << jo << " = " << swz_expr("jt", xs) << ";\n";
   }
   bool first = true;
+  // who writes and who reads each buffer position in this exchange
+  const std::vector<uint8_t> wown = owners(xs);
+  set_layout(t.ecmask);
+  const std::vector<uint8_t> rown = owners(xs);
+  std::copy(saved_slot, saved_slot + 4, slot_);
+  std::copy(saved_thr, saved_thr + 16, thr_);
   each([&]() {
+    const int xi = xb_;
     const char* X = xb_ ? "XB" : "XA";
     xb_ ^= 1;
     std::copy(saved_slot, saved_slot + 4, slot_);  // barrier groups compare with the current layout
     std::copy(saved_thr, saved_thr + 16, thr_);
-    const std::string bar = barrier_for(t.ecmask);
+    if (!exchange_safe(xi, wown)) {
+      // a warp of another group may still use this buffer's positions from
+      // an earlier exchange: wait for the whole block first
+      o_ << "    __syncthreads();  // earlier users of this buffer are not ordered before these writes\n";
+      next_bar_ = 1;
+      xhist_.clear();
+    }
+    uint32_t gmask = 0;
+    const std::string bar = barrier_for(t.ecmask, &gmask);
+    if (!gmask) xhist_.clear();
+    xhist_.push_back(XRec{xi, gmask != 0, wown, rown, gmask});
     if (adj_) o_ << "    { const uint32_t sj = " << jo << ";\n";
     else o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
     for (int e = 0; e < R_; ++e)

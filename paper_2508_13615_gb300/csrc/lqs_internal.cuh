@@ -136,6 +136,15 @@ struct PlanCfg {
   int max_ops = 0; // per-segment cap
 };
 int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* arith);
+// Tensor-core dense blocks (block_tc.cu): lowered ops confined to qubits
+// 0..kBlockQubits-1 composed into one 32x32 complex matrix (row-major
+// interleaved, qubit q = bit q of the local index), applied to a complex64
+// state in one pass; block_weight is an op's share of a run's dense work (a
+// run goes to the tensor cores when its weights reach the threshold).
+constexpr int kBlockQubits = 5;
+void block_matrix(const std::vector<KOp>& ops, const std::vector<int>& idx, double* U);
+int apply_block(SV* sv, const double* U);
+double block_weight(const KOp& op);
 // The configuration lqs_autotune_fused chose for this circuit structure, if any.
 bool tuned_cfg(int n, int dtype, const lqs_op* ops, int n_ops, lqs_fuse_cfg* out);
 int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::vector<Segment>& segs);

@@ -51,7 +51,7 @@ class lqs_pauli(ctypes.Structure):
 
 class lqs_fuse_cfg(ctypes.Structure):
     _fields_ = [("tile_qubits", ctypes.c_int32), ("low_qubits", ctypes.c_int32), ("arith", ctypes.c_int32),
-                ("max_ops", ctypes.c_int32)]
+                ("max_ops", ctypes.c_int32), ("tc_blocks", ctypes.c_int32)]
 
 
 class lqs_batch_item(ctypes.Structure):
@@ -215,6 +215,7 @@ def _cfg(cfg) -> Optional[lqs_fuse_cfg]:
     c.low_qubits = int(cfg.get("low_qubits", 0))
     c.arith = int(cfg.get("arith", 0))
     c.max_ops = int(cfg.get("max_ops", 0))
+    c.tc_blocks = int(cfg.get("tc_blocks", 0))
     return c
 
 

@@ -110,3 +110,51 @@ def test_block_arguments_are_checked():
         bad[3, 4] = np.nan
         with pytest.raises(L.LqsError):
             L.lqs_apply_block(sv.h, 5, bad)
+
+
+def _merged_circuit(n, seed):
+    """Gates on qubits 0..4 (the block window) interleaved with gates on
+    qubits 5..n-1, and every 40 ops a gate joining both sides (it ends a
+    run): the fused path must move the outside gates past each run."""
+    a = W.random_circuit(5, 160, seed=seed)
+    b = W.random_circuit(n - 5, 70, seed=seed + 1)
+    c = W.Circuit(n)
+    c.params = np.concatenate([a.params, b.params, [0.7, -1.3]])
+    off = len(a.params)
+    ia = ib = 0
+    k = 0
+    while ia < len(a.ops) or ib < len(b.ops):
+        if ia < len(a.ops) and (k % 3 != 2 or ib >= len(b.ops)):
+            c.ops.append(a.ops[ia])
+            ia += 1
+        elif ib < len(b.ops):
+            o = b.ops[ib]
+            c.ops.append(W.Op(o.name, tuple(w + 5 for w in o.wires), o.pidx + off if o.pidx >= 0 else -1,
+                              o.matrix, o.inverse))
+            ib += 1
+        k += 1
+        if k % 40 == 0:
+            c.ops.append(W.Op("CRY", (4, 7 + k % (n - 7)), len(c.params) - 2, None, False))
+            c.ops.append(W.Op("CNOT", (9, 2), -1, None, False))
+    return c
+
+
+@pytest.mark.parametrize("n", [14, 17])
+def test_fused_path_extracts_tensor_core_blocks(n):
+    """lqs_apply_fused on complex64 applies heavy runs on qubits 0..4 as
+    tensor-core blocks (and only when allowed); both ways match the oracle."""
+    L = _lib()
+    c = _merged_circuit(n, 300 + n)
+    psi0 = W.gaussian_state(n, 301 + n)
+    want = oracle.run_circuit(c, psi0)
+    got = {}
+    for mode, cfg in (("on", {"tc_blocks": 4}), ("off", {"tc_blocks": -1})):
+        with gpu_state(n, "c64", psi0) as sv:
+            L.lqs_profile_start()
+            sv.apply(c, fused=True, cfg=cfg)
+            recs = L.lqs_profile_stop()
+            got[mode] = sv.numpy()
+        blocks = sum(1 for r in recs if r[0].startswith("k_block_tc"))
+        assert (blocks > 0) == (mode == "on"), (mode, blocks)
+        assert max_abs(got[mode], want) <= TOL["c64"], mode
+    assert max_abs(got["on"], got["off"]) <= TOL["c64"]

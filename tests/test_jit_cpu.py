@@ -159,6 +159,102 @@ def _bank_model(src):
     return extra
 
 
+def _unordered_accesses(src):
+    """Shared-memory accesses of a generated kernel's tile loop that conflict
+    (same exchange-buffer position, different warps, at least one a write)
+    without a chain of barriers ordering them.  The loop body is replayed from
+    its source: exchange writes and reads with their swizzled positions per
+    thread, and every barrier with the warp groups it joins (a named barrier
+    joins the warps agreeing on its tid bits, __syncwarp one warp,
+    __syncthreads all)."""
+    import re
+
+    def swz(j, sz):
+        return j ^ ((((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7) if sz == 16 else (((j >> 4) ^ (j >> 8)) & 15))
+
+    def pfold(j, *m):
+        return sum((bin(j & mb).count("1") & 1) << b for b, mb in enumerate(m))
+
+    def ev(expr, **kw):
+        expr = re.sub(r"(0x[0-9a-f]+)u", r"\1", expr)
+        expr = re.sub(r"(\d+)u\b", r"\1", expr)
+        expr = re.sub(r"lqs::jit::swz<(\d+)>\((\w+)\)", r"swz(\2, \1)", expr).replace("lqs::jit::pfold", "pfold")
+        return eval(expr, {"swz": swz, "pfold": pfold}, kw)
+
+    nth = int(re.search(r"__launch_bounds__\((\d+),", src).group(1))
+    nw = nth // 32
+    body = src.split("for (; t < G.ntiles; t += gridDim.x) {", 1)[1]
+    events = []  # ("bar", key(warp)) or ("acc", buf, is_write, {position: warp})
+    jt = named = None
+    named = {}
+    sj = None
+    cur = None
+    for line in body.splitlines():
+        s = line.strip()
+        m = re.match(r"(?:uint32_t )?jt = (.*);$", s)
+        if m:
+            jt = [ev(m.group(1), tid=t) for t in range(nth)]
+            continue
+        m = re.match(r"const uint32_t (jo\d+) = (.*);$", s)
+        if m:
+            named[m.group(1)] = [ev(m.group(2), jt=jt[t]) for t in range(nth)]
+            continue
+        m = re.match(r"\{ const uint32_t sj = (.*);$", s)
+        if m:
+            sj = named[m.group(1)] if m.group(1) in named else [ev(m.group(1), jt=jt[t]) for t in range(nth)]
+            cur = None
+            continue
+        m = re.search(r"(st_w|ld_w)\(&(X[AB])\[sj \^ (0x[0-9a-f]+)u\]", s)
+        if m and sj is not None:
+            wr, buf, c = m.group(1) == "st_w", m.group(2), int(m.group(3), 16)
+            if cur is None or cur[1] != buf or cur[2] != wr:
+                cur = ["acc", buf, wr, {}]
+                events.append(cur)
+            for t in range(nth):
+                cur[3][sj[t] ^ c] = t // 32
+            continue
+        if s.startswith("}"):
+            sj = None
+            cur = None
+        if "__syncthreads" in s:
+            events.append(("bar", lambda w: 0))
+        elif "__syncwarp" in s:
+            events.append(("bar", lambda w: w))
+        else:
+            m = re.search(r"bar_group\((\d+)u(.*), (\d+)u\);", s)
+            if m:
+                bits = [int(b) for b in re.findall(r"tid >> (\d+)", m.group(2))]
+                events.append(("bar", lambda w, bits=tuple(bits): tuple(((w * 32) >> b) & 1 for b in bits)))
+
+    def ordered(v, i1, w, i2):
+        seen = {v}
+        for e in events[i1 + 1:i2]:
+            if e[0] == "bar":
+                keys = {e[1](u) for u in seen}
+                seen = {x for x in range(nw) if e[1](x) in keys}
+        return w in seen
+
+    bad = []
+    last = {}  # (buf, pos) -> (last write (warp, i), [reads since])
+    for i, e in enumerate(events):
+        if e[0] != "acc":
+            continue
+        _, buf, wr, own = e
+        for pos, w in own.items():
+            lw, rs = last.get((buf, pos), (None, []))
+            deps = ([lw] if lw else []) + (rs if wr else [])
+            for v, j in deps:
+                if v != w and not ordered(v, j, w, i):
+                    bad.append((buf, pos, v, j, w, i))
+            if wr:
+                last[(buf, pos)] = ((w, i), [])
+            else:
+                last[(buf, pos)] = (lw, rs + [(w, i)])
+        if len(bad) > 20:
+            break
+    return bad
+
+
 def test_exchanges_are_bank_conflict_free(tmp_path, monkeypatch):
     """Every layout exchange of generated kernels (forward and adjoint, both
     amplitude sizes) writes and reads shared memory without bank conflicts:
@@ -176,3 +272,6 @@ def test_exchanges_are_bank_conflict_free(tmp_path, monkeypatch):
     assert files
     bad = {f: e for f in files for e in [_bank_model(open(f).read())] if e}
     assert not bad, bad
+    # and every pair of conflicting exchange accesses is ordered by barriers
+    races = {f: r[:3] for f in files for r in [_unordered_accesses(open(f).read())] if r}
+    assert not races, races
