@@ -622,6 +622,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", action="store_true",
+                    help="let lqs_autotune_fused pick the tile shapes first (measured: +0.4%% for 45 s of tuning)")
     ap.add_argument("--config", default="main",
                     choices=["main", "adjoint24", "precision32", "batch256", "sweep30", "tcblock30"],
                     help="secondary measurements (one JSON line each); the default is the headline run")
@@ -665,6 +667,15 @@ def main():
     n_jit = sum(L.lqs_jit_precompile(n, "c128", c.ops, c.params, L.LQS_ARITH_DF) for c in (wl.ansatz, wl.qft))
     n_jit += L.lqs_jit_precompile_expval(n, "c128", wl.tfim, False, L.LQS_ARITH_DF)
     jit_s = time.perf_counter() - t_jit
+    # The tile shape per circuit structure, chosen once by the library's
+    # autotuner (lqs_apply_fused then uses it); the autotuner uses the state as
+    # scratch, and every step starts from the saved input.
+    t_tune = time.perf_counter()
+    tuned = {}
+    if args.tune:
+        for name, c, ops in (("ansatz", wl.ansatz, wl.ans_ops), ("qft", wl.qft, wl.qft_ops)):
+            tuned[name] = L.lqs_autotune_fused(wl.sv.h, ops, c.params, repeats=1)
+    tune_s = time.perf_counter() - t_tune
 
     for _ in range(args.warmup):
         wl.step()
@@ -747,6 +758,7 @@ def main():
             "gb_per_s_algorithmic": bytes_step / (ms_step * 1e-3) / 1e9,
             "hbm_frac_of_8TBps": bytes_step / (ms_step * 1e-3) / 8e12,
             "energy_tfim_ansatz": wl.energy,
+            "autotuned": {"configs": tuned, "wall_s": round(tune_s, 2)} if tuned else None,
             "segment_compiler": {"mode": "on", "structures_compiled": n_jit, "compile_wall_s": round(jit_s, 2),
                                  "compiled_launches_timed": jit1["launches"] - jit0["launches"],
                                  "compiled_during_timed": jit1["compiled"] - jit0["compiled"],
