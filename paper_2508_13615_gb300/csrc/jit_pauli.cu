@@ -35,7 +35,7 @@ namespace lqs {
 
 namespace {
 
-constexpr int kPauliWordsJit = 32;
+constexpr int kPauliWordsJit = 64;
 constexpr int kPauliThreadBits = 8;
 
 std::string hx(uint64_t x) {
@@ -145,13 +145,26 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
       o << "    lqs::jit::gput(" << it->second << ", (tid & 31u) == " << (zt & 31u) << "u, " << sg << ", wacc + warp * "
         << nw << " + " << w << ");\n";
     }
-    // X/Y words: pairs with the lowest X bit clear
+    // X/Y words: pairs with the lowest X bit clear.  Their warp sums go four
+    // at a time through one reduce-scatter (gflush4).
+    std::vector<std::pair<std::string, int>> pend;
+    auto flush = [&](bool all) {
+      while (pend.size() >= 4 || (all && !pend.empty())) {
+        o << "    lqs::jit::gflush4(";
+        for (int i = 0; i < 4; ++i) o << (i < (int)pend.size() ? pend[i].first : "lqs::jit::GAcc<A>::zero()") << ", ";
+        for (int i = 0; i < 4; ++i)
+          o << (i < (int)pend.size() ? "wacc + warp * " + std::to_string(nw) + " + " + std::to_string(pend[i].second)
+                                     : std::string("(double*)0"))
+            << (i < 3 ? ", " : ");\n");
+        pend.erase(pend.begin(), pend.begin() + std::min<size_t>(4, pend.size()));
+      }
+    };
     for (int w = 0; w < nw; ++w) {
       const JWord& W = ws[w];
       if (!W.xl) continue;
       const uint32_t zt = W.zl & tmask, zr = W.zl >> tb;
       const std::string acc = "g" + std::to_string(uid++);
-      o << "    { lqs::jit::GAcc<A>::T " << acc << " = lqs::jit::GAcc<A>::zero();\n";
+      o << "    lqs::jit::GAcc<A>::T " << acc << " = lqs::jit::GAcc<A>::zero();\n    {\n";
       const bool lowreg = W.lowbit >= tb;
       if (!lowreg) o << "      if (!((tid >> " << W.lowbit << ") & 1u)) {\n";
       const std::string st = x_(thread_sign(zt), tile_sign(W.ze));
@@ -168,8 +181,11 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
         }
       }
       if (!lowreg) o << "      }\n";
-      o << "      lqs::jit::gflush(" << acc << ", wacc + warp * " << nw << " + " << w << ");\n    }\n";
+      o << "    }\n";
+      pend.emplace_back(acc, w);
+      flush(false);
     }
+    flush(true);
   }
   if (lam) {
     // diagonal words: one signed coefficient sum per amplitude
