@@ -166,21 +166,47 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
       const std::string acc = "g" + std::to_string(uid++);
       o << "    lqs::jit::GAcc<A>::T " << acc << " = lqs::jit::GAcc<A>::zero();\n    {\n";
       const bool lowreg = W.lowbit >= tb;
-      if (!lowreg) o << "      if (!((tid >> " << W.lowbit << ") & 1u)) {\n";
-      const std::string st = x_(thread_sign(zt), tile_sign(W.ze));
-      for (int e = 0; e < R; ++e) {
-        if (lowreg && ((e >> (W.lowbit - tb)) & 1)) continue;
-        const bool cneg = __builtin_popcount(e & zr) & 1;
-        const std::string neg = cneg ? "!" + std::string("(") + st + ")" : st;
-        const std::string c = partner(e, W.xl), bself = val(e);
+      // the pair term of representative j (lowest X bit of j clear):
+      // c = psi_{j ^ x}, b = psi_j, sign of j's Z bits
+      auto term = [&](const std::string& c, const std::string& b, const std::string& neg) {
         switch (W.ph) {
-          case 0: o << "        lqs::jit::gre<A>(" << acc << ", " << c << ", " << bself << ", " << neg << ");\n"; break;
-          case 1: o << "        lqs::jit::gim<A>(" << acc << ", " << c << ", " << bself << ", !(" << neg << "));\n"; break;
-          case 2: o << "        lqs::jit::gre<A>(" << acc << ", " << c << ", " << bself << ", !(" << neg << "));\n"; break;
-          default: o << "        lqs::jit::gim<A>(" << acc << ", " << c << ", " << bself << ", " << neg << ");\n"; break;
+          case 0: o << "        lqs::jit::gre<A>(" << acc << ", " << c << ", " << b << ", " << neg << ");\n"; break;
+          case 1: o << "        lqs::jit::gim<A>(" << acc << ", " << c << ", " << b << ", !(" << neg << "));\n"; break;
+          case 2: o << "        lqs::jit::gre<A>(" << acc << ", " << c << ", " << b << ", !(" << neg << "));\n"; break;
+          default: o << "        lqs::jit::gim<A>(" << acc << ", " << c << ", " << b << ", " << neg << ");\n"; break;
         }
+      };
+      const std::string st = x_(thread_sign(zt), tile_sign(W.ze));
+      auto neg_at = [&](int e, const std::string& s_) {
+        return (__builtin_popcount(e & zr) & 1) ? "!(" + s_ + ")" : s_;
+      };
+      if (!lowreg && W.lowbit >= 5 && r >= 1) {
+        // a warp bit: the two warps of each pair share the pairs (split by
+        // the top register bit) instead of one of them idling; the other
+        // warp forms the same terms from its side (its own register is the
+        // partner value c, the representative's amplitude comes from XA, and
+        // the sign is taken at the representative, tid ^ x)
+        const int ms = r - 1;
+        const uint32_t xt = W.xl & tmask, xr = W.xl >> tb;
+        const std::string sx = thread_sign(zt);
+        const std::string st1 = x_((__builtin_popcount(xt & zt) & 1) ? "!" + sx : sx, tile_sign(W.ze));
+        o << "      if (!((tid >> " << W.lowbit << ") & 1u)) {\n";
+        for (int e = 0; e < R; ++e)
+          if (!((e >> ms) & 1)) term(partner(e, W.xl), val(e), neg_at(e, st));
+        o << "      } else {\n";
+        for (int e = 0; e < R; ++e)
+          if ((e >> ms) & 1)
+            term(val(e ^ (int)xr), "lqs::ld_w(&XA[(tid ^ " + std::to_string(xt) + "u) + " + std::to_string(e << tb) + "u])",
+                 neg_at(e, st1));
+        o << "      }\n";
+      } else {
+        if (!lowreg) o << "      if (!((tid >> " << W.lowbit << ") & 1u)) {\n";
+        for (int e = 0; e < R; ++e) {
+          if (lowreg && ((e >> (W.lowbit - tb)) & 1)) continue;
+          term(partner(e, W.xl), val(e), neg_at(e, st));
+        }
+        if (!lowreg) o << "      }\n";
       }
-      if (!lowreg) o << "      }\n";
       o << "    }\n";
       pend.emplace_back(acc, w);
       flush(false);
