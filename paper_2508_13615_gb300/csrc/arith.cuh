@@ -237,6 +237,7 @@ struct ArF32 {
     }
     return make_float2(re, im);
   }
+  static LQS_HD W cmac4_raw(const C* c, const W* a) { return cmac4(c, a); }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) { return make_float2(c0 * a.x + c1 * b.x, c0 * a.y + c1 * b.y); }
   static LQS_HD C kmul(C a, C b) { return cmul(a, b); }
   static LQS_HD C cconst1() { return make_float2(1.f, 0.f); }
@@ -277,6 +278,7 @@ struct ArF64 {
     }
     return make_double2(re, im);
   }
+  static LQS_HD W cmac4_raw(const C* c, const W* a) { return cmac4(c, a); }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) { return make_double2(c0 * a.x + c1 * b.x, c0 * a.y + c1 * b.y); }
   static LQS_HD C kmul(C a, C b) { return cmul(a, b); }
   static LQS_HD C cconst1() { return make_double2(1.0, 0.0); }
@@ -334,6 +336,22 @@ struct ArDF {
       df_mac(im, a[k].re, c[k].im);
     }
     return DFC{df_norm(re), df_norm(im)};
+  }
+  // cmac4 without the final renormalisation, for results that go straight
+  // to float64 storage (df2d rounds hi + lo however they are split)
+  static LQS_HD W cmac4_raw(const C* c, const W* a) {
+    DAcc re = df_prod(a[0].re, c[0].re);
+    df_mac(re, df_neg(a[0].im), c[0].im);
+    DAcc im = df_prod(a[0].im, c[0].re);
+    df_mac(im, a[0].re, c[0].im);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      df_mac(re, a[k].re, c[k].re);
+      df_mac(re, df_neg(a[k].im), c[k].im);
+      df_mac(im, a[k].im, c[k].re);
+      df_mac(im, a[k].re, c[k].im);
+    }
+    return DFC{DF{re.s, re.e}, DF{im.s, im.e}};
   }
   static LQS_HD W rmac2(R c0, W a, R c1, W b) {
     DAcc re = df_prod(a.re, c0);

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_dense2(typename A::S* __restrict__
 #pragma unroll
     for (int r = 0; r < 4; ++r) x[r] = A::load(s[r]);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) psi[id[r]] = A::store(A::cmac4(&M.c[4 * r], x));
+    for (int r = 0; r < 4; ++r) psi[id[r]] = A::store(A::cmac4_raw(&M.c[4 * r], x));
   }
 }
 
