@@ -100,6 +100,49 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# ranks: one process per GPU, independent replicas
+# ---------------------------------------------------------------------------
+class Ranks:
+    """The processes of a torchrun launch (RANK / WORLD_SIZE / LOCAL_RANK).
+    The path does not shard: each rank runs a full replica, and ranks share
+    only a barrier around the timed region and the slowest rank's time."""
+
+    def __init__(self, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float, device: str) -> float:
+        """The largest x over all ranks."""
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self) -> None:
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def replicas_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed by the slowest rank."""
+    return units_per_rank * world / seconds
+
+
+# ---------------------------------------------------------------------------
 # the workload
 # ---------------------------------------------------------------------------
 class Workload:
@@ -641,18 +684,10 @@ def main():
         return
 
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ranks = Ranks("nccl")
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     import paper_2508_13615_gb300 as L
     pk = peaks()
@@ -698,13 +733,9 @@ def main():
     jit1 = L.lqs_jit_info()
     clk = clocks.stop()
     barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = ranks.max(e0.elapsed_time(e1), "cuda")
     ms_step = ms / args.steps
-    value = wl.gates * world / (ms_step * 1e-3)
+    value = replicas_value(wl.gates, world, ms_step * 1e-3)
     bytes_step = sum(r[2] for r in records) / args.steps
     roof, fams = roofline(records, pk)
 
@@ -717,11 +748,7 @@ def main():
         barrier()
         t0 = time.perf_counter()
         pipe.run(args.steps)
-        et = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([et], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = ranks.max(time.perf_counter() - t0, "cuda")
         pipe.close()
         sample = out_host[::max(1, out_host.size // 4096)].copy()
         # one more step with nothing overlapped, timed part by part (after the measured ones)
@@ -733,7 +760,7 @@ def main():
             fn()
             torch.cuda.synchronize()
             parts[key] = round(1e3 * (time.perf_counter() - tp), 1)
-        e2e = {"value": wl.gates * world * args.steps / et, "unit": UNIT,
+        e2e = {"value": replicas_value(wl.gates * args.steps, world, et), "unit": UNIT,
                "h2d_bytes_per_step": wl.input_bytes(), "d2h_bytes_per_step": int(out_host.nbytes) + 8,
                "ms_per_step": 1e3 * et / args.steps, "parts_ms_sequential_step": parts,
                "pipelined_result_matches_sequential":
@@ -767,8 +794,7 @@ def main():
             "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(rec), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
