@@ -12,9 +12,18 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "jit.h"
 #include "lqs_internal.cuh"
 #include "tile.cuh"
 #include "tile_ops.cuh"
+
+// Dense work per segment: a compiled segment is straight-line code, and one
+// whose dense updates add up past this weight (4 per two-qubit dense op, 1
+// per one-qubit dense op; diagonal and permutation ops are free) spends more
+// in instruction fetch than a further pass costs.
+#ifndef LQS_SEGMENT_DENSE_CAP
+#define LQS_SEGMENT_DENSE_CAP 16
+#endif
 
 namespace lqs {
 
@@ -26,6 +35,8 @@ int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* ari
   pc.k = reg_tile_qubits(dtype);                  // the register-tile kernel's shape
   pc.b = dtype == LQS_C64 ? 5 : 4;
   pc.max_ops = kMaxTileOps;
+  // multi-tile states whose segments run as compiled code
+  pc.dense_cap = n > reg_tile_qubits(dtype) && jit_enabled_for(n) ? LQS_SEGMENT_DENSE_CAP : 0;
   int ar = LQS_ARITH_AUTO;
   if (cfg) {
     if (cfg->tile_qubits) pc.k = cfg->tile_qubits;
@@ -74,6 +85,10 @@ static int coef_count(const KOp& o) {
 // non-diagonal targets fit the tile, adding qubits while fewer than k are
 // used.  Diagonal ops and controls need no tile qubit.  An op that is not
 // taken blocks its wires for the rest of the segment.
+static int dense_weight(const KOp& o) {
+  return o.kind == K_DENSE2 ? 4 : (o.kind == K_DENSE1 || o.kind == K_DENSE1R) ? 1 : 0;
+}
+
 int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::vector<Segment>& segs) {
   const int k = std::min(pc.k, n), b = std::min(pc.b, k);
   const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
@@ -85,7 +100,7 @@ int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::ve
     while (done[first]) ++first;
     Segment seg;
     uint64_t Q = low, blocked = 0;
-    int ncoef = 0;
+    int ncoef = 0, dense = 0;
     for (size_t i = first; i < ops.size() && blocked != all; ++i) {
       if (done[i]) continue;
       const KOp& o = ops[i];
@@ -96,14 +111,17 @@ int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::ve
       }
       const uint64_t need = o.tile_mask() & ~Q;
       const int nc = coef_count(o);
+      const int dw = dense_weight(o);
       const bool fits = __builtin_popcountll(Q | need) <= k && (int)seg.ops.size() < pc.max_ops &&
-                        ncoef + nc <= kMaxTileCoef;
+                        ncoef + nc <= kMaxTileCoef &&
+                        (pc.dense_cap <= 0 || dense + dw <= pc.dense_cap || seg.ops.empty());
       if (fits) {
         Q |= need;
         seg.ops.push_back((int)i);
         done[i] = 1;
         --remaining;
         ncoef += nc;
+        dense += dw;
       } else {
         blocked |= wires;
       }

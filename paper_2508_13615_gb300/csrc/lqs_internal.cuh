@@ -131,9 +131,10 @@ struct Segment {
   std::vector<int> ops;         // indices into the lowered op list, in execution order
 };
 struct PlanCfg {
-  int k = 0;       // tile qubits
-  int b = 0;       // low contiguous qubits
-  int max_ops = 0; // per-segment cap
+  int k = 0;          // tile qubits
+  int b = 0;          // low contiguous qubits
+  int max_ops = 0;    // per-segment cap
+  int dense_cap = 0;  // cap on a segment's dense weight (compiled segments; 0 = none)
 };
 int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* arith);
 // Tensor-core dense blocks (block_tc.cu): lowered ops confined to qubits
