@@ -581,6 +581,45 @@ def config_sweep30(args):
     print(json.dumps({"config": "sweep30", "n_qubits": n, "state_bytes": S, "rows": rows}), flush=True)
 
 
+def config_universal30(args):
+    """The universal circuit of Sec. 3.2 (Fig. 6a: 2 n^2 gates, phase gates
+    and CNOT ladders) at 30 qubits complex128: fused (compiled segments)
+    against the plain per-gate path."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    n = args.n
+    c = W.universal(n)
+    L.lqs_set_jit(L.LQS_JIT_ON)
+    L.lqs_jit_precompile(n, "c128", c.ops, c.params, L.LQS_ARITH_DF)
+    sv = L.StateVector(n, "c128")
+    st = torch.cuda.current_stream()
+    ops = L.OpArray(c.ops)
+
+    def t_of(fn, reps=3):
+        L.lqs_sv_set_basis(sv.h, 1)
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            L.lqs_sv_set_basis(sv.h, 1)
+            e0, e1 = _events()
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    ms_fused = t_of(lambda: L.lqs_apply_fused(sv.h, ops, c.params, None))
+    ms_plain = t_of(lambda: sv.apply(c, fused=False), reps=1)
+    passes = L.lqs_plan_fused(n, "c128", c.ops)[0]
+    print(json.dumps({"config": "universal30", "n_qubits": n, "dtype": "c128", "gates": len(c.ops),
+                      "fused_ms": ms_fused, "fused_passes": passes, "fused_gates_per_s": len(c.ops) / (ms_fused * 1e-3),
+                      "plain_ms": ms_plain, "plain_gates_per_s": len(c.ops) / (ms_plain * 1e-3),
+                      "speedup_fused": ms_plain / ms_fused}), flush=True)
+    sv.close()
+
+
 def config_tcblock30(args):
     """Dense 32x32 blocks on the tensor cores at 30 qubits complex64: one
     block pass (tcgen05 3xTF32) against the same run of gates on the fused
@@ -668,7 +707,7 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="let lqs_autotune_fused pick the tile shapes first (measured: +0.4%% for 45 s of tuning)")
     ap.add_argument("--config", default="main",
-                    choices=["main", "adjoint24", "precision32", "batch256", "sweep30", "tcblock30"],
+                    choices=["main", "adjoint24", "precision32", "batch256", "sweep30", "tcblock30", "universal30"],
                     help="secondary measurements (one JSON line each); the default is the headline run")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -680,7 +719,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         {"adjoint24": config_adjoint24, "precision32": config_precision32, "batch256": config_batch256,
-         "sweep30": config_sweep30, "tcblock30": config_tcblock30}[args.config](args)
+         "sweep30": config_sweep30, "tcblock30": config_tcblock30, "universal30": config_universal30}[args.config](args)
         return
 
     import torch

@@ -292,3 +292,19 @@ def test_orthogonal_2x2_forms_at_edge_angles(jit_on, dtype, arith):
         err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
     assert err <= TOL[dtype], err
     assert L.lqs_jit_info()["launches"] > before["launches"]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n", [13, 16])
+def test_universal_circuit_vs_oracle(jit_on, dtype, arith, n):
+    """The universal circuit of Sec. 3.2 (2 n^2 phase gates and CNOTs) from a
+    Gaussian state, on the fused (compiled) and the plain path."""
+    set_mode(arith)
+    c = W.universal(n)
+    psi0 = W.gaussian_state(n, 500 + n)
+    want = oracle.run_circuit(c, psi0)
+    for fused in (True, False):
+        with gpu_state(n, dtype, psi0) as sv:
+            sv.apply(c, fused=fused)
+            err = max_abs(sv.numpy(), want)
+        assert err <= TOL[dtype], (fused, err)

@@ -407,9 +407,18 @@ def test_paper_facts():
             if o.name != "H":
                 k = abs(o.wires[1] - o.wires[0])
                 assert W.qft(n, swaps=False).params[o.pidx] == math.pi / 2 ** k
-    # universal-circuit gate count identity 2N^2 = N(N-1) + N(N+1)
+    # universal-circuit gate count identity 2N^2 = N(N-1) + N(N+1), and the
+    # generator's counts and R_k angles (pi / 2^k)
     for N in range(1, 42):
         assert 2 * N * N == N * (N - 1) + N * (N + 1)
+    uc = facts["universal_circuit"]
+    for N in (2, 5, 30, 38):
+        c = W.universal(N)
+        assert len(c.ops) == eval(uc["total"], {"N": N})
+        assert sum(o.name == "CNOT" for o in c.ops) == eval(uc["cnot"], {"N": N})
+        assert sum(o.name == "PhaseShift" for o in c.ops) == eval(uc["rk"], {"N": N})
+        ks = {round(math.log2(math.pi / c.params[o.pidx])) for o in c.ops if o.name == "PhaseShift"}
+        assert ks <= set(range(1, N + 1))
     # single-gate sweep fixes the CNOT control at 24 (t = 24 uses control 0)
     sw = W.sweep_30q()
     cn = [c for name, c in sw if name.startswith("CNOT")]
@@ -499,4 +508,30 @@ def test_dense_block_of_a_product_is_the_product():
     psi = rand_state(n, 40)
     got = oracle.apply_matrix(psi.copy(), n, wires, np.kron(Ua, Ub))
     want = oracle.apply_matrix(oracle.apply_matrix(psi.copy(), n, wires[3:], Ub), n, wires[:3], Ua)
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+@pytest.mark.parametrize("n,x", [(5, 0b10110), (7, 0b1001101), (9, 0)])
+def test_universal_circuit_on_basis_states(n, x):
+    """Every gate of the universal circuit is a phase or a permutation, so a
+    basis state stays one basis state times a phase: each layer multiplies by
+    e^{i phi} for every qubit whose bit is 1, then the CNOT ladder
+    0 -> 1 -> ... -> n-1 replaces bit q+1 by (bit q) xor (bit q+1) in order.
+    Tracked with integer bit operations, independently of the oracle."""
+    c = W.universal(n)
+    state, phase = x, 0.0
+    i = 0
+    for layer in range(n + 1):
+        for q in range(n):
+            if (state >> q) & 1:
+                phase += c.params[c.ops[i].pidx]
+            i += 1
+        if layer < n:
+            for q in range(n - 1):
+                if (state >> q) & 1:
+                    state ^= 1 << (q + 1)
+            i += n - 1
+    want = np.zeros(1 << n, dtype=complex)
+    want[state] = np.exp(1j * phase)
+    got = oracle.run_circuit(c, oracle.basis_state(n, x))
     assert np.max(np.abs(got - want)) < 1e-13

@@ -247,6 +247,26 @@ def qft(n_qubits: int, swaps: bool = True) -> Circuit:
     return c
 
 
+def universal(n_qubits: int) -> Circuit:
+    """The N-qubit universal circuit of Sec. 3.2 (Fig. 6a) with phase gates:
+    N layers of [R_k on every qubit, then the CNOT ladder 0 -> 1 -> ... ->
+    N-1], then R_k on every qubit once more; R_k is the phase gate of angle
+    pi / 2^k (PhaseShift), with k = 1 + (layer + qubit) mod N.  That is
+    N (N + 1) R_k's and N (N - 1) CNOTs, 2 N^2 gates."""
+    n = n_qubits
+    c = Circuit(n)
+    vals = []
+    for layer in range(n + 1):
+        for q in range(n):
+            c.ops.append(Op("PhaseShift", (q,), len(vals)))
+            vals.append(math.pi / float(1 << (1 + (layer + q) % n)))
+        if layer < n:
+            for q in range(n - 1):
+                c.ops.append(Op("CNOT", (q, q + 1)))
+    c.params = np.asarray(vals, dtype=np.float64)
+    return c
+
+
 def ghz(n_qubits: int) -> Circuit:
     """H on qubit 0 followed by the CNOT ladder: (|0..0> + |1..1>)/sqrt(2)."""
     c = Circuit(n_qubits)
