@@ -382,7 +382,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-# secondary configurations (one JSON line each; not the driver's default run)
+# secondary configurations (one JSON line each; not part of the default run)
 # ---------------------------------------------------------------------------
 def _events():
     import torch
