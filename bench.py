@@ -276,7 +276,7 @@ ALU_PEAK_TFLOPS = {"df": FP32_INSTR_PEAK / DF_INSTR_PER_FLOP / 1e12, "f32": 2 * 
 # summarised in profiles/compiled_segment_ansatz_24q_c128.md (24 qubits,
 # scaled by the 64x units of a 30-qubit launch).  Retake it when the kernels
 # change.
-TRAFFIC = {"k_fused_reg_jit/df": {"bytes_per_launch": (268.6e6 + 206.5e6) * 64,
+TRAFFIC = {"k_fused_reg_jit/df": {"bytes_per_launch": (268.6e6 + 213.3e6) * 64,
                                   "source": "profiles/compiled_segment_ansatz_24q_c128.md (24 q capture x 64)"}}
 
 
