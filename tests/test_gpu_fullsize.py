@@ -1,5 +1,5 @@
 """Parity at the benchmark's full size: 30 qubits, complex128, the launch
-configuration bench.py times.
+configuration bench.py times (compiled fused segments and Pauli passes).
 
 The oracle cannot run whole 30-qubit circuits in test time, so each check
 uses something it can compute at this size:
@@ -30,12 +30,15 @@ def big():
     import torch
     import paper_2508_13615_gb300 as L
     set_mode("df")
+    old = L.lqs_jit_info()["mode"]
+    L.lqs_set_jit(L.LQS_JIT_ON)  # as bench.py runs: fused segments and Pauli passes compiled
     psi = W.gaussian_state(N_Q, 2)  # the bench's P1 input
     sv = L.StateVector(N_Q, "c128")
     sv.from_numpy(psi)
     saved = sv.tensor.clone()
     yield L, torch, psi, sv, saved
     sv.close()
+    L.lqs_set_jit(old)
 
 
 def sample_indices(seed, count=4096):
@@ -88,8 +91,10 @@ def test_qft_30q_fused_closed_form_and_tfim(big):
 def test_ansatz_30q_fused_matches_plain(big):
     L, torch, psi, sv, saved = big
     c = W.ansatz(N_Q, 10, 3)
+    before = L.lqs_jit_info()["launches"]
     sv.set_basis(0)
     sv.apply(c, fused=True)
+    assert L.lqs_jit_info()["launches"] > before  # the compiled segments ran
     idx = sample_indices(11)
     fused = gather(torch, sv, idx)
     assert abs(sv.norm2() - 1.0) <= 1e-11
