@@ -624,7 +624,8 @@ def config_tcblock30(args):
     """Dense 32x32 blocks on the tensor cores at 30 qubits complex64: one
     block pass (tcgen05 3xTF32) against the same run of gates on the fused
     path (40 Haar U4 gates on neighbouring pairs of qubits 0..4, compiled
-    segments), with the block's matrix formed on the host from the gates."""
+    segments, block extraction off), with the block's matrix formed on the
+    host from the gates; and the same gates with the planner's extraction on."""
     import torch
     import paper_2508_13615_gb300 as L
     n = args.n
@@ -670,13 +671,15 @@ def config_tcblock30(args):
     ref = sv.tensor.clone()
     ms_block = t_of(lambda: L.lqs_apply_block(sv.h, 5, U))
     ops = L.OpArray(c.ops)
-    ms_fused = t_of(lambda: L.lqs_apply_fused(sv.h, ops, c.params, None))
+    alu = {"tc_blocks": -1}  # the gates on the compiled fused path (no block extraction)
+    ms_fused = t_of(lambda: L.lqs_apply_fused(sv.h, ops, c.params, alu))
+    ms_auto = t_of(lambda: L.lqs_apply_fused(sv.h, ops, c.params, None))  # the planner extracts the block
     # one application each from the same input, compared
     sv.tensor.copy_(ref)
     L.lqs_apply_block(sv.h, 5, U)
     a = sv.tensor.clone()
     sv.tensor.copy_(ref)
-    L.lqs_apply_fused(sv.h, ops, c.params, None)
+    L.lqs_apply_fused(sv.h, ops, c.params, alu)
     diff = float((a - sv.tensor).abs().max().item())
     scale = float(sv.tensor.abs().max().item())
     S = (1 << n) * 8
@@ -689,7 +692,7 @@ def config_tcblock30(args):
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / pk["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"},
         "tensor_tflops": flops / (ms_block * 1e-3) / 1e12,
-        "fused_gates": len(c.ops), "fused_ms": ms_fused,
+        "fused_gates": len(c.ops), "fused_ms": ms_fused, "fused_with_block_extraction_ms": ms_auto,
         "speedup_vs_fused": ms_fused / ms_block,
         "max_abs_diff_block_vs_fused": diff, "max_abs_amplitude": scale}), flush=True)
     sv.close()

@@ -24,6 +24,10 @@
 #ifndef LQS_SEGMENT_DENSE_CAP
 #define LQS_SEGMENT_DENSE_CAP 16
 #endif
+// complex64 segments carry float32 arithmetic, several times less code per op
+#ifndef LQS_SEGMENT_DENSE_CAP_C64
+#define LQS_SEGMENT_DENSE_CAP_C64 64
+#endif
 
 namespace lqs {
 
@@ -36,7 +40,9 @@ int resolve_cfg(int n, int dtype, const lqs_fuse_cfg* cfg, PlanCfg& pc, int* ari
   pc.b = dtype == LQS_C64 ? 5 : 4;
   pc.max_ops = kMaxTileOps;
   // multi-tile states whose segments run as compiled code
-  pc.dense_cap = n > reg_tile_qubits(dtype) && jit_enabled_for(n) ? LQS_SEGMENT_DENSE_CAP : 0;
+  pc.dense_cap = n > reg_tile_qubits(dtype) && jit_enabled_for(n)
+                     ? (dtype == LQS_C64 ? LQS_SEGMENT_DENSE_CAP_C64 : LQS_SEGMENT_DENSE_CAP)
+                     : 0;
   int ar = LQS_ARITH_AUTO;
   if (cfg) {
     if (cfg->tile_qubits) pc.k = cfg->tile_qubits;
