@@ -766,9 +766,12 @@ int note_reg_prog(int n, int dtype, int arith, const std::vector<KOp>& ops, cons
 // Measured on GB300 (24-qubit ansatz): complex128 runs fastest with 4
 // amplitudes of each state per thread and 256 threads (half the code per
 // op, 16 warps per SM), complex64 with 16 per state and 128 threads.
+#ifndef LQS_ADJ_THREAD_BITS_C128
+#define LQS_ADJ_THREAD_BITS_C128 9
+#endif
 static void adj_shape(int dtype, int* r, int* tb) {
   *r = dtype == LQS_C64 ? 4 : 2;
-  *tb = dtype == LQS_C64 ? 7 : 8;
+  *tb = dtype == LQS_C64 ? 7 : LQS_ADJ_THREAD_BITS_C128;
 }
 int adjoint_tile_qubits(int dtype) {
   int r, tb;

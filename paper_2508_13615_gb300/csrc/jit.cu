@@ -1134,10 +1134,10 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   s << "};\n";
   std::string head = replace_all(kSkeletonHead, "@NAME@", kname);
   head = replace_all(head, "@NTH@", std::to_string(nth));
-  // resident CTAs per SM the register budget aims at: forward 2 x 256
-  // threads; adjoint 3 x 128, or with 256 threads 2 (4 amplitudes of each
-  // state per thread) or 1 (8 or more)
-  const int minb = !adj_ ? std::max(1, 512 / nth) : nth <= 128 ? 3 : (R_ * sz_ <= 64 ? 2 : 1);
+  // resident CTAs per SM the register budget aims at: forward 512 threads
+  // per SM; adjoint 3 x 128, with 256 threads 2 (4 amplitudes of each state
+  // per thread) or 1 (8 or more), with 512 threads 1
+  const int minb = !adj_ ? std::max(1, 512 / nth) : nth <= 128 ? 3 : nth >= 512 ? 1 : (R_ * sz_ <= 64 ? 2 : 1);
   head = replace_all(head, "@MINB@", std::to_string(minb));
   head = replace_all(head, "@LAMP@", adj_ ? "A::S* __restrict__ lam, " : "");
   head = replace_all(head, "@PARTP@", adj_ ? "double* partial, " : "");
