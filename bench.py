@@ -690,7 +690,10 @@ def config_tcblock30(args):
         "block": "32x32 complex on qubits 0..4, tcgen05.mma kind::tf32, 3xTF32",
         "block_ms": ms_block, "block_gbs": gbs,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / pk["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"},
+                     "frac": gbs / pk["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+                     # DRAM read + write of one launch at 26 qubits (ncu), scaled by the 16x units of 30 qubits
+                     "traffic": (537.0e6 + 475.1e6) * (1 << (n - 26)),
+                     "traffic_source": "profiles/k_block_tc_tf32x3_26q_c64.md (26 q capture x 2^(n-26))"},
         "tensor_tflops": flops / (ms_block * 1e-3) / 1e12,
         "fused_gates": len(c.ops), "fused_ms": ms_fused, "fused_with_block_extraction_ms": ms_auto,
         "speedup_vs_fused": ms_fused / ms_block,
