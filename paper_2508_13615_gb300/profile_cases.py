@@ -10,7 +10,8 @@ expectation, three times), ``adjoint`` (adjoint gradient of a 2-layer
 ansatz), ``gate`` (one dense H per qubit on the plain path), ``u4`` (the
 Haar 4x4 gates of the single-gate sweep, U4(t, t+1), on the plain path),
 ``block`` (a Haar 32x32 block on qubits 0..4 on the tensor cores, three
-times; complex64 only).  States start at
+times; complex64 only), ``rz`` (one RZ per qubit) and ``cnot`` (CNOT from the
+highest qubit to every other one), both on the plain path.  States start at
 |0..0>; the sizes default to 24 qubits so the state (256 MiB complex128)
 exceeds the 129 MB L2 while a full ncu capture stays short.
 """
@@ -60,6 +61,14 @@ def main(argv=None) -> None:
         L.lqs_apply_gate(sv.h, "H", (0,))
         for _ in range(3):
             L.lqs_apply_block(sv.h, 5, U)
+    elif mode == "rz":
+        sv.apply_gate("H", (0,))
+        for q in range(n):
+            sv.apply_gate("RZ", (q,), (0.3 + 0.1 * q,))
+    elif mode == "cnot":
+        sv.apply_gate("H", (n - 1,))
+        for q in range(n - 1):
+            sv.apply_gate("CNOT", (n - 1, q))
     elif mode == "u4":
         for _, c in W.sweep_30q(n):
             if c.ops[0].name == "U4":
