@@ -199,6 +199,14 @@ LQS_API int lqs_apply_matrix(lqs_sv* sv, const int* wires, int n_wires, const do
  * a device-side timeout is reported by lqs_sv_sync (LQS_ERR_TIMEOUT). */
 LQS_API int lqs_apply_block(lqs_sv* sv, int m, const double* matrix);
 
+/* The 32x32 matrix of a run of gates on qubits 0..4 (every wire < 5), as
+ * lqs_apply_fused composes the runs it sends to the tensor cores: the ops
+ * applied in order to each of the 32 basis states of five qubits.  Written to
+ * `matrix` (row-major interleaved complex128, 2 * 32 * 32 doubles, host) in
+ * the layout lqs_apply_block takes.  Host only; LQS_ERR_ARG on a bad op or a
+ * wire >= 5. */
+LQS_API int lqs_block_matrix(const lqs_op* ops, int n_ops, const double* params, int n_params, double* matrix);
+
 /* Fused path: the host planner groups the circuit into segments whose
  * non-diagonal targets fit one tile of 2^k amplitudes (low contiguous qubits
  * plus chosen high qubits); each segment is one HBM pass in which the tile is

@@ -450,6 +450,17 @@ int apply_block(SV* sv, const double* matrix) {
 
 using namespace lqs;
 
+extern "C" int lqs_block_matrix(const lqs_op* ops, int n_ops, const double* params, int n_params, double* matrix) {
+  if (!matrix) return set_error(LQS_ERR_ARG, "matrix is NULL");
+  if (n_ops < 0 || (n_ops > 0 && !ops)) return set_error(LQS_ERR_ARG, "bad ops");
+  std::vector<KOp> kops;
+  LQS_TRY(lower_ops(kBlockQubits, ops, n_ops, params, n_params, false, kops));  // wires must be < 5
+  std::vector<int> idx(kops.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  block_matrix(kops, idx, matrix);
+  return LQS_OK;
+}
+
 extern "C" int lqs_apply_block(lqs_sv* h, int m, const double* matrix) {
   void* dptr = nullptr;
   int n = 0, dtype = 0;

@@ -94,6 +94,7 @@ def _load():
         "lqs_sv_copy_to_host": (i32, [vp, vp]),
         "lqs_sv_copy_to_host_async": (i32, [vp, vp]),
         "lqs_apply_block": (i32, [vp, ctypes.c_int, vp]),
+        "lqs_block_matrix": (i32, [vp, ctypes.c_int, vp, ctypes.c_int, vp]),
         "lqs_sv_sync": (i32, [vp]),
         "lqs_apply_gate": (i32, [vp, i32, ip, i32, dp, i32, i32]),
         "lqs_apply_matrix": (i32, [vp, ip, i32, dp]),
@@ -275,6 +276,16 @@ def lqs_apply_block(h, m: int, matrix) -> None:
     if U.shape != (1 << m, 1 << m):
         raise ValueError("matrix must be 2^m x 2^m")
     _check(_L.lqs_apply_block(h, int(m), U.ctypes.data))
+
+
+def lqs_block_matrix(ops, params) -> np.ndarray:
+    """The 32x32 complex matrix of a run of gates on qubits 0..4 (host only)."""
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    p = _params(params)
+    out = np.zeros((32, 32), dtype=np.complex128)
+    _check(_L.lqs_block_matrix(oa.ptr(), oa.n, _dptr(p), int(np.asarray(params).size) if params is not None else 0,
+                               out.ctypes.data))
+    return out
 
 
 def lqs_sv_sync(h) -> None:
