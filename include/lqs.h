@@ -169,6 +169,15 @@ LQS_API int lqs_sv_copy_to_host_async(const lqs_sv* sv, void* host);
  * errors (LQS_ERR_CUDA) and device-side wait timeouts (LQS_ERR_TIMEOUT). */
 LQS_API int lqs_sv_sync(lqs_sv* sv);
 
+/* Exercises the device-side timeout path: enqueues one kernel that waits, with
+ * the bounded wait every tile-loading kernel uses, on a shared-memory barrier
+ * that nothing completes.  Each such wait gives up after 2^22 polls or 2 s of
+ * the GPU's global timer, whichever comes first, flags the handle's status and
+ * returns, so the next lqs_sv_sync returns LQS_ERR_TIMEOUT (and clears the
+ * flag); the context and the state stay usable.  No amplitude is read or
+ * written. */
+LQS_API int lqs_check_bounded_wait(lqs_sv* sv);
+
 /* ---- gates --------------------------------------------------------------------- */
 
 /* Plain per-gate path: one kernel for one gate, chosen by gate class

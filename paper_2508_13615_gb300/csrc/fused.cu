@@ -360,3 +360,28 @@ template void init_prog<ArF64>(TileProg<ArF64>&, int, uint64_t, int, int);
 template void init_prog<ArDF>(TileProg<ArDF>&, int, uint64_t, int, int);
 
 }  // namespace lqs
+
+namespace lqs {
+
+// One thread waits, with the kernels' bounded wait, on a shared-memory barrier
+// that expects one arrival and never gets it; the wait gives up and flags the
+// status exactly as a tile load that never landed would.  No copy is issued.
+__global__ void k_wait_for_nothing(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait(&bar, 0)) flag_timeout(status, 16);
+}
+
+}  // namespace lqs
+
+extern "C" int lqs_check_bounded_wait(lqs_sv* h) {
+  void* dptr = nullptr;
+  int n = 0, dtype = 0;
+  LQS_TRY(lqs_sv_info(h, &dptr, &n, &dtype));  // validates the handle
+  lqs::SV* sv = reinterpret_cast<lqs::SV*>(h);
+  lqs::k_wait_for_nothing<<<1, 1, 0, sv->stream>>>(sv->d_status);
+  LQS_CUDA_TRY(cudaGetLastError());
+  lqs::count_launch();
+  return LQS_OK;
+}

@@ -23,7 +23,8 @@ constexpr int kMaxTileCoef = 448;
 constexpr int kMaxTileBits = 14;
 constexpr int kTileThreads = 256;
 constexpr int kTileWarps = kTileThreads / 32;
-constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier waits (well under a minute), then error flag
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier waits: at most this many polls ...
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // ... and at most 2 s of the global timer, then error flag
 
 struct TileGeom {
   int n, k, b, r;
@@ -112,10 +113,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait: false when the limit was reached (the caller flags an error).
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false when it gave up (the caller flags an error).  A poll
+// may suspend the thread for a hardware-chosen time, so besides the poll count
+// the global timer bounds the wait: it is read every 64 polls, and the wait
+// gives up once kWaitLimitNs have passed since the first reading.  A wait that
+// completes within 63 polls never reads it.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+  uint64_t t0 = 0;
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u) {
+      const uint64_t now = globaltimer_ns();
+      if (it == 63u) t0 = now;
+      else if (now - t0 > kWaitLimitNs) return false;
+    }
+  }
   return false;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {

@@ -96,6 +96,7 @@ def _load():
         "lqs_apply_block": (i32, [vp, ctypes.c_int, vp]),
         "lqs_block_matrix": (i32, [vp, ctypes.c_int, vp, ctypes.c_int, vp]),
         "lqs_sv_sync": (i32, [vp]),
+        "lqs_check_bounded_wait": (i32, [vp]),
         "lqs_apply_gate": (i32, [vp, i32, ip, i32, dp, i32, i32]),
         "lqs_apply_matrix": (i32, [vp, ip, i32, dp]),
         "lqs_apply_fused": (i32, [vp, ctypes.POINTER(lqs_op), i32, dp, i32, ctypes.POINTER(lqs_fuse_cfg)]),
@@ -290,6 +291,11 @@ def lqs_block_matrix(ops, params) -> np.ndarray:
 
 def lqs_sv_sync(h) -> None:
     _check(_L.lqs_sv_sync(h))
+
+
+def lqs_check_bounded_wait(h) -> None:
+    """Enqueues a kernel whose bounded wait gives up; the next lqs_sv_sync(h) raises LQS_ERR_TIMEOUT."""
+    _check(_L.lqs_check_bounded_wait(h))
 
 
 def lqs_apply_gate(h, gate, wires: Sequence[int], params=(), inverse: bool = False) -> None:

@@ -1,5 +1,8 @@
 """Edge cases of the GPU path against the oracle: empty circuits, the
-smallest states, degenerate observables and circuits without parameters."""
+smallest states, degenerate observables, circuits without parameters, and a
+device-side wait that runs out."""
+import time
+
 import numpy as np
 import pytest
 
@@ -71,3 +74,26 @@ def test_adjoint_without_parameters(dtype):
     assert len(g) == 0
     assert abs(e - oracle.energy(c, terms)) <= (1e-11 if dtype == "c128" else 2e-5)
     assert max_abs(back, oracle.basis_state(n, 0)) <= TOL[dtype]
+
+
+def test_bounded_wait_gives_up_and_the_state_stays_usable():
+    """A kernel waits on a barrier that nothing completes: its bounded wait gives
+    up (after 2^22 polls or 2 s of the global timer), the next sync reports LQS_ERR_TIMEOUT once,
+    and the same handle then runs a circuit that matches the oracle."""
+    import paper_2508_13615_gb300 as L
+    set_mode("df")
+    n = 12
+    c = W.random_circuit(n, 40, seed=620)
+    with gpu_state(n, "c128", basis=0) as sv:
+        sv.sync()
+        t0 = time.perf_counter()
+        L.lqs_check_bounded_wait(sv.h)
+        with pytest.raises(L.LqsError) as err:
+            sv.sync()
+        waited = time.perf_counter() - t0
+        assert err.value.code == L.lqs.LQS_ERR_TIMEOUT and "gave up" in str(err.value)
+        print(f"bounded wait gave up after {waited:.2f} s")
+        assert waited <= 30.0
+        sv.sync()  # the flag was cleared
+        sv.apply(c, fused=True)
+        assert max_abs(sv.numpy(), oracle.run_circuit(c)) <= TOL["c128"]
