@@ -25,6 +25,7 @@ def test_alu_bound_family_is_judged_against_the_double_float_roof():
     assert out["hbm_frac_of_measured"] == pytest.approx(34.36e9 / 20e-3 / 1e9 / 6000.0)
     assert out["share"] == pytest.approx(80.0 / 90.0)
     assert out["ms_per_launch"] == pytest.approx(20.0) and out["bytes_per_launch"] == pytest.approx(34.36e9)
+    assert out["traffic"] is None  # no ncu capture is stored for this family
     assert fams["k_gate/df"]["launches"] == 2 and fams["k_gate/df"]["GBps"] == pytest.approx(34.36e9 / 5e-3 / 1e9, rel=1e-3)
 
 
@@ -46,3 +47,17 @@ def test_derived_double_float_peak():
 def test_replicas_value_is_whole_job_throughput():
     assert bench.replicas_value(1490, 1, 1.5) == pytest.approx(1490 / 1.5)
     assert bench.replicas_value(1490, 8, 1.5) == pytest.approx(8 * 1490 / 1.5)
+
+
+def test_traffic_of_the_dominant_kernel():
+    pk = {"hbm_gbs": 6691.5}
+    name = "k_fused_reg_jit/df"
+    out, _ = bench.roofline([(name, 20.0, 34.36e9, 120e12)], pk)
+    t = bench.TRAFFIC[name]
+    assert out["traffic_source"] == t["source"]
+    if t.get("changed_since"):
+        assert out["traffic"] is None and out["traffic_last_capture"] == t["bytes_per_launch"]
+    else:
+        assert out["traffic"] == t["bytes_per_launch"]
+    out, _ = bench.roofline([(name, 20.0, 34.36e9, 120e12)], pk, traffic=1.5e9)
+    assert out["traffic"] == 1.5e9
