@@ -7,14 +7,14 @@ of Sec. 3.1 of arxiv 2508.13615) in plain C complex128 (``lqs_oracle.c``), and
 this module only marshals arguments and sequences calls.
 
 Parity status per function (what pins each, see ``tests/test_oracle_pins.py``):
-  gate_matrix / apply_gate / run_circuit  -- Kronecker-product brute force,
-      matrix exponentials of the Pauli generators, gate identities, GHZ and QFT
-      closed forms, numpy FFT.
-  expval                                   -- explicit Kronecker Pauli matrices,
-      eigenstates with known eigenvalues.
-  param_shift_grad                         -- central finite differences and the
-      analytic derivative of closed-form one-qubit expectations.
-  apply_gate_at                            -- the full update at the same indices.
+  gate_matrix / op_matrix / apply_matrix / apply_op / run_circuit
+      -- Kronecker-product brute force, matrix exponentials of the Pauli
+      generators, gate identities, GHZ and QFT closed forms, numpy FFT.
+  norm2 / expval / energy  -- explicit Kronecker Pauli matrices, eigenstates
+      with known eigenvalues.
+  param_shift_grad  -- central finite differences and the analytic derivative
+      of closed-form one-qubit expectations.
+  apply_matrix_at / apply_op_at  -- the full update at the same indices.
 """
 from __future__ import annotations
 
