@@ -98,3 +98,30 @@ def test_df_flushes_tiny_and_keeps_zero():
     out = L.lqs_debug_df_roundtrip(x)[:, 1]
     np.testing.assert_array_equal(out[:4], 0.0)
     assert out[4] == 2.0 ** -102
+
+
+def test_every_handle_call_rejects_a_null_handle_before_any_device_work():
+    """Each entry point that takes a state handle returns LQS_ERR_ARG for NULL
+    (checked first, so this holds on a machine without a GPU)."""
+    R = B._L
+    d = ctypes.c_double()
+    calls = {
+        "lqs_sv_info": lambda: R.lqs_sv_info(None, None, None, None),
+        "lqs_sv_set_basis": lambda: R.lqs_sv_set_basis(None, 0),
+        "lqs_sv_copy_from_host": lambda: R.lqs_sv_copy_from_host(None, None),
+        "lqs_sv_copy_to_host": lambda: R.lqs_sv_copy_to_host(None, None),
+        "lqs_sv_copy_to_host_async": lambda: R.lqs_sv_copy_to_host_async(None, None),
+        "lqs_sv_sync": lambda: R.lqs_sv_sync(None),
+        "lqs_check_bounded_wait": lambda: R.lqs_check_bounded_wait(None),
+        "lqs_apply_gate": lambda: R.lqs_apply_gate(None, 3, None, 0, None, 0, 0),
+        "lqs_apply_matrix": lambda: R.lqs_apply_matrix(None, None, 0, None),
+        "lqs_apply_fused": lambda: R.lqs_apply_fused(None, None, 0, None, 0, None),
+        "lqs_apply_block": lambda: R.lqs_apply_block(None, 5, None),
+        "lqs_norm2": lambda: R.lqs_norm2(None, ctypes.byref(d)),
+        "lqs_expval": lambda: R.lqs_expval(None, None, 0, ctypes.byref(d), None),
+        "lqs_adjoint_grad": lambda: R.lqs_adjoint_grad(None, None, 0, None, 0, None, 0, None, None),
+        "lqs_sv_distance": lambda: R.lqs_sv_distance(None, None, ctypes.byref(d), ctypes.byref(d)),
+        "lqs_autotune_fused": lambda: R.lqs_autotune_fused(None, None, 0, None, 0, 1, None),
+    }
+    for name, call in calls.items():
+        assert call() == B.LQS_ERR_ARG, name
