@@ -125,3 +125,24 @@ def test_every_handle_call_rejects_a_null_handle_before_any_device_work():
     }
     for name, call in calls.items():
         assert call() == B.LQS_ERR_ARG, name
+
+
+def test_static_expval_and_batch_validate_their_arguments():
+    """Argument checks of the allocation-free expectation value and of the
+    batched driver, which run before any device work.  The fake device address
+    is only ever validated, never used: the test runs only without a GPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import workloads as W
+    R = B._L
+    d = ctypes.c_double()
+    fake = ctypes.c_void_p(256)
+    assert R.lqs_expval_static(None, 10, 1, None, None, 0, ctypes.byref(d), None) == B.LQS_ERR_ARG
+    many = B.PauliArray(W.tfim(30) + [W.pauli_word(1.0, {q: "Z"}) for q in range(6)])  # 65 words
+    assert R.lqs_expval_static(fake, 30, 1, None, many.ptr(), many.n, ctypes.byref(d), None) == B.LQS_ERR_ARG
+    assert "at most 64" in L.lqs_last_error()
+    outside = B.PauliArray([W.pauli_word(1.0, {31: "Z"})])
+    assert R.lqs_expval_static(fake, 30, 1, None, outside.ptr(), outside.n, ctypes.byref(d), None) == B.LQS_ERR_ARG
+    assert R.lqs_expval_static(fake, 37, 1, None, None, 0, ctypes.byref(d), None) == B.LQS_ERR_ARG
+    assert R.lqs_batch_run(None, 3, 1, None) == B.LQS_ERR_ARG
