@@ -1,4 +1,10 @@
 // C ABI entry points (include/lqs.h): validation, handles, dispatch.
+//
+// The calls follow the paper's circuit model: gates from its gate set applied
+// to qubits of one state (Sec. 2, Sec. 3.2), expectation values of a
+// Hamiltonian given as a sum of Pauli words and gradients with respect to the
+// gate parameters (Listing 1).  Each gate is routed by class and by the
+// qubits it touches (Sec. 2, Fig. 1).
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -1,5 +1,6 @@
 // Autotuner for the fused path: picks the tile shape and segment length of
 // lqs_apply_fused for a circuit structure by timing candidates on the GPU.
+// The paper has no tuner; its kernels are fixed per gate class (Sec. 2).
 //
 // The register-tile kernels fix the tile width k (the registers and thread
 // bits of a thread block); what varies is the number b of low contiguous

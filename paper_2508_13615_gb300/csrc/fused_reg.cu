@@ -1,8 +1,12 @@
 // Register-resident tile kernel for fused segments.
 //
-// A tile of 2^k amplitudes (k = r + 8) is spread over 256 threads with
+// The paper keeps gates on a process's local qubits free of communication
+// (Sec. 2, Fig. 1a); here the qubits of a tile held on chip play that role,
+// and a run of gates on them costs one HBM pass.
+//
+// A tile of 2^k amplitudes (k = r + 9) is spread over 512 threads with
 // R = 2^r amplitudes in each thread's registers.  A "layout" assigns r of the
-// tile's k local qubits to register index bits and the other 8 to thread
+// tile's k local qubits to register index bits and the other 9 to thread
 // index bits.  A gate whose non-diagonal targets are register qubits is pure
 // register arithmetic: no shared memory, no barrier, no index math beyond
 // compile-time register indices.  Controls and diagonal factors on any qubit

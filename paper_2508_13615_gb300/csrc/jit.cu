@@ -1,5 +1,6 @@
 // Segment compiler: a fused segment's register-tile program, compiled into a
-// straight-line kernel.
+// straight-line kernel.  The gates are the paper's pair and quad updates on
+// local qubits (Sec. 2, Fig. 1a), here on the qubits of a tile held on chip.
 //
 // The register-tile interpreter (fused_reg.cu) reads each op of a segment at
 // run time: its kind, its register slot, its control pattern and its

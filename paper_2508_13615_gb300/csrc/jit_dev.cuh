@@ -1,4 +1,6 @@
-// Device helpers for runtime-compiled segment kernels.
+// Device helpers for runtime-compiled segment kernels: the pair and quad
+// updates of gates on local qubits (Sec. 2, Fig. 1a) written for a tile held
+// in registers.
 //
 // A compiled segment is straight-line code: every register index, layout,
 // control pattern and coefficient offset is a constant of its source, so the

@@ -1,6 +1,8 @@
 // Pieces shared by the measurement, adjoint and batched kernels: double-float
 // inner products, Pauli-word descriptions and their pass planning, adjoint
-// generator partials, and inverse ops.
+// generator partials, and inverse ops.  The measured quantity is the
+// expectation of a Hamiltonian given as a sum of Pauli words, and the
+// differentiated one its gradient in the gate parameters (Listing 1).
 #pragma once
 #include <algorithm>
 #include <vector>

@@ -1,4 +1,6 @@
-// Allocation-free expectation value (lqs_expval_static).
+// Allocation-free expectation value (lqs_expval_static): the expectation of
+// a Hamiltonian given as a sum of Pauli words (Listing 1), without any device
+// allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
 // measurement: code that runs while a CUDA stream is being captured into a
