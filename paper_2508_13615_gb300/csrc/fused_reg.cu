@@ -763,13 +763,14 @@ int note_reg_prog(int n, int dtype, int arith, const std::vector<KOp>& ops, cons
 // ---------------------------------------------------------------------------
 // compiled adjoint (reverse sweep over psi and lambda)
 // ---------------------------------------------------------------------------
-// Tiles one qubit smaller than the forward kernel's, with 128 threads: the
-// kernel holds two states in registers and four tiles in shared memory
-// (incoming psi and lambda, two exchange buffers), three CTAs per SM.
+// The kernel holds two states in registers and four tiles in shared memory
+// (incoming psi and lambda, two exchange buffers), so its tiles are smaller
+// than the forward kernel's: 2^11 amplitudes for both dtypes.
 // Shape of the compiled adjoint: register bits per state and thread bits.
 // Measured on GB300 (24-qubit ansatz): complex128 runs fastest with 4
-// amplitudes of each state per thread and 256 threads (half the code per
-// op, 16 warps per SM), complex64 with 16 per state and 128 threads.
+// amplitudes of each state per thread and 512 threads, one CTA per SM (half
+// the code per op of 8 amplitudes; 256 threads were 3% slower), complex64
+// with 16 per state and 128 threads, three CTAs per SM.
 #ifndef LQS_ADJ_THREAD_BITS_C128
 #define LQS_ADJ_THREAD_BITS_C128 9
 #endif
