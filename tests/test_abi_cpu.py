@@ -146,3 +146,25 @@ def test_static_expval_and_batch_validate_their_arguments():
     assert R.lqs_expval_static(fake, 30, 1, None, outside.ptr(), outside.n, ctypes.byref(d), None) == B.LQS_ERR_ARG
     assert R.lqs_expval_static(fake, 37, 1, None, None, 0, ctypes.byref(d), None) == B.LQS_ERR_ARG
     assert R.lqs_batch_run(None, 3, 1, None) == B.LQS_ERR_ARG
+
+
+def test_every_device_wait_goes_through_the_bounded_wait():
+    """The only mbarrier poll in the sources is the one inside the bounded wait
+    (tile.cuh's mbar_wait, limited by a poll count and the global timer), and
+    no kernel source spins on a flag in memory."""
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_13615_gb300", "csrc")
+    polls = []
+    for name in sorted(os.listdir(csrc)):
+        if not name.endswith((".cu", ".cuh", ".h")):
+            continue
+        with open(os.path.join(csrc, name)) as f:
+            src = f.read()
+        for m in re.finditer(r"mbarrier\.(try_wait|test_wait)", src):
+            polls.append(name)
+        assert not re.search(r"while\s*\(\s*\*?\s*(volatile|flag|ld_acquire)", src), name
+    assert polls == ["tile.cuh"]
+    with open(os.path.join(csrc, "tile.cuh")) as f:
+        tile = f.read()
+    body = tile[tile.index("bool mbar_wait("):]
+    body = body[: body.index("\n}\n")]
+    assert "kSpinLimit" in body and "kWaitLimitNs" in body and "globaltimer_ns()" in body
