@@ -10,6 +10,10 @@ One step is one pass of the whole hot path over one batch of synthetic input:
       (890 gates), then <TFIM> = <sum Z_i Z_i+1 + 0.5 sum X_i>;
   P3  the 30-qubit QFT of a seeded basis state on the fused path (480 gates).
 Metric: gates/s (1490 gates per step) with the step's algorithmic HBM GB/s.
+The same line carries the metric's other two parts: the step run again in
+complex64 (its gates/s, and its energy and states against complex128's), and
+the adjoint gradient's time over one forward pass on the 24-qubit, 8-layer,
+384-parameter TFIM circuit in both precisions, with a central-difference check.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the same workload (one sweep gate per step) on the host cores instead.
@@ -146,12 +150,13 @@ def replicas_value(units_per_rank: float, world: int, seconds: float) -> float:
 # the workload
 # ---------------------------------------------------------------------------
 class Workload:
-    def __init__(self, n: int, psi_host):
+    def __init__(self, n: int, psi_host, dtype: str = "c128"):
         import torch
 
         import paper_2508_13615_gb300 as L
         self.L = L
         self.n = n
+        self.dtype = dtype
         self.sweep = W.sweep_30q(n)
         self.ansatz = W.ansatz(n, 10, 3)
         self.qft = W.qft(n)
@@ -166,13 +171,23 @@ class Workload:
             p = op.matrix if op.name in ("U2", "U4") else (c.params if len(c.params) else ())
             self.sweep_calls.append((op.name, op.wires, p))
         self.gates = len(self.sweep) + len(self.ansatz.ops) + len(self.qft.ops)
-        self.sv = L.StateVector(n, "c128")
+        self.sv = L.StateVector(n, dtype)
         self.saved = torch.empty_like(self.sv.tensor)
         self.psi_host = psi_host
         L.lqs_sv_copy_from_host(self.sv.h, psi_host)
         self.saved.copy_(self.sv.tensor)
         torch.cuda.synchronize()
         self.energy = None
+
+    def precompile(self, arith) -> int:
+        """Compiles the fused segments and Pauli passes of P2 and P3 (host only)."""
+        L = self.L
+        k = sum(L.lqs_jit_precompile(self.n, self.dtype, c.ops, c.params, arith) for c in (self.ansatz, self.qft))
+        return k + L.lqs_jit_precompile_expval(self.n, self.dtype, self.tfim, False, arith)
+
+    def close(self) -> None:
+        self.sv.close()
+        self.saved = None
 
     def input_bytes(self) -> int:
         b = self.psi_host.nbytes
@@ -204,32 +219,41 @@ class Workload:
 class E2EPipeline:
     """The step end to end through the C ABI with host buffers.
 
-    Every step copies its input state from pinned host memory, runs P1 on it,
-    reads the result back into pinned host memory, and runs P2 (energy read
-    back to the host) and P3 on a second state.  Uploads and read-backs run on
-    streams of their own into two alternating device buffers, so step i+1's
-    upload and step i's read-back overlap step i's compute; all of their bytes
-    still cross inside the timed region (the first upload is fully exposed)."""
+    Every step copies its input state from pinned host memory, runs P1 on it
+    and reads P1's output state back into pinned host memory, then runs P2
+    (the energy is read back to the host by lqs_expval) and P3 on a second
+    state and reads P3's output state back as well.  Uploads and read-backs
+    run on streams of their own into alternating device buffers, so step
+    i+1's upload and step i's read-backs overlap step i's compute; all of
+    their bytes still cross inside the timed region (the first upload and the
+    last read-back are fully exposed)."""
 
-    def __init__(self, wl: Workload, out_host):
+    def __init__(self, wl: Workload, out_p1, out_p3):
         import torch
         L = wl.L
-        self.wl, self.out_host = wl, out_host
+        self.wl, self.out_p1, self.out_p3 = wl, out_p1, out_p3
         self.sc, self.sh, self.sd = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
         self.buf = [torch.empty_like(wl.sv.tensor) for _ in range(2)]
+        self.wbuf = [torch.empty_like(wl.sv.tensor) for _ in range(2)]
         # one library handle per (buffer, stream) it is used on
-        self.comp = [L.StateVector(wl.n, "c128", tensor=b, stream=self.sc) for b in self.buf]
-        self.up = [L.StateVector(wl.n, "c128", tensor=b, stream=self.sh) for b in self.buf]
-        self.down = [L.StateVector(wl.n, "c128", tensor=b, stream=self.sd) for b in self.buf]
-        self.work = L.StateVector(wl.n, "c128", stream=self.sc)
+        self.comp = [L.StateVector(wl.n, wl.dtype, tensor=b, stream=self.sc) for b in self.buf]
+        self.up = [L.StateVector(wl.n, wl.dtype, tensor=b, stream=self.sh) for b in self.buf]
+        self.down = [L.StateVector(wl.n, wl.dtype, tensor=b, stream=self.sd) for b in self.buf]
+        self.work = [L.StateVector(wl.n, wl.dtype, tensor=b, stream=self.sc) for b in self.wbuf]
+        self.work_down = [L.StateVector(wl.n, wl.dtype, tensor=b, stream=self.sd) for b in self.wbuf]
         torch.cuda.synchronize()
+
+    def d2h_bytes_per_step(self) -> int:
+        return int(self.out_p1.nbytes) + int(self.out_p3.nbytes) + 8  # two states and the energy
 
     def run(self, steps: int) -> None:
         import torch
         L, wl = self.wl.L, self.wl
         up = [torch.cuda.Event() for _ in range(steps)]
         p1 = [torch.cuda.Event() for _ in range(steps)]
+        p3 = [torch.cuda.Event() for _ in range(steps)]
         down = [torch.cuda.Event() for _ in range(steps)]
+        down3 = [torch.cuda.Event() for _ in range(steps)]
 
         def upload(i):
             if i >= 2:  # the buffer is free once step i-2's read-back is done
@@ -245,48 +269,96 @@ class E2EPipeline:
             wl.p1(self.comp[i % 2].h)
             p1[i].record(self.sc)
             self.sd.wait_event(p1[i])
-            L.lqs_sv_copy_to_host_async(self.down[i % 2].h, self.out_host)
+            L.lqs_sv_copy_to_host_async(self.down[i % 2].h, self.out_p1)
             down[i].record(self.sd)
-            wl.p2p3(self.work.h)
+            if i >= 2:  # the work buffer is free once step i-2's P3 read-back is done
+                self.sc.wait_event(down3[i - 2])
+            wl.p2p3(self.work[i % 2].h)
+            p3[i].record(self.sc)
+            self.sd.wait_event(p3[i])
+            L.lqs_sv_copy_to_host_async(self.work_down[i % 2].h, self.out_p3)
+            down3[i].record(self.sd)
         for s in (self.sc, self.sh, self.sd):
             s.synchronize()
 
     def close(self) -> None:
-        for sv in self.comp + self.up + self.down + [self.work]:
+        for sv in self.comp + self.up + self.down + self.work + self.work_down:
             sv.close()
-        self.buf = None
+        self.buf = self.wbuf = None
 
 
-# Peaks derived from the unit counts and clocks of the part (152 SMs, 128 FP32
-# lanes per SM, 2.07 GHz maximum SM clock): 40.3 T FP32 instructions/s.  The
-# double-float complex128 gate math of the compiled segments costs 32 FP32
-# instructions per amplitude for a real 2x2 (6 flops): each of the two real
+# A secondary, derived arithmetic figure for the double-float kernels (it is
+# not a chip peak): 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3 T FP32
+# instructions/s, divided by the FP32 instructions this code's double-float
+# complex128 gate math spends per float64-equivalent flop.  A real 2x2 update
+# costs 32 FP32 instructions per amplitude (6 flops): each of the two real
 # outputs is two products with their exact error terms (8), one TwoSum (6)
-# and two error additions, renormalised only every 16 updates.  That is 5.33
-# instructions per float64-equivalent flop, so the arithmetic peak is
-# 40.3 / 5.33 = 7.6 TFLOP/s float64-equivalent; native complex64 math is 2
-# flops per FMA lane-cycle.
+# and two error additions.  That is 5.33 instructions per flop, so the
+# derived figure is 40.3 / 5.33 = 7.6 TFLOP/s float64-equivalent.  Native
+# complex64 math is 2 flops per FMA lane-cycle.
 FP32_INSTR_PEAK = 152 * 128 * 2.07e9
 DF_INSTR_PER_FLOP = 32.0 / 6.0
 ALU_PEAK_TFLOPS = {"df": FP32_INSTR_PEAK / DF_INSTR_PER_FLOP / 1e12, "f32": 2 * FP32_INSTR_PEAK / 1e12,
                    "f64": 1.25}
 
 
-# DRAM traffic per launch of the dominant kernel family, from the ncu capture
-# summarised in profiles/compiled_segment_ansatz_24q_c128.md (24 qubits,
-# scaled by the 64x units of a 30-qubit launch).  A capture taken before the
-# kernels last changed is reported as `traffic_last_capture`, with `traffic`
-# null, until it is retaken.
-KERNELS_CHANGED_SINCE_CAPTURE = ("the tile loads' bounded mbarrier wait gained a global-timer limit after these "
-                                 "counters were taken; the data movement is unchanged")
-TRAFFIC = {"k_fused_reg_jit/df": {"bytes_per_launch": (268.6e6 + 213.3e6) * 64,
-                                  "source": "profiles/compiled_segment_ansatz_24q_c128.md (24 q capture x 64)",
-                                  "changed_since": KERNELS_CHANGED_SINCE_CAPTURE}}
+def sources_digest(paths) -> str:
+    """sha256 (first 16 hex digits) of the listed repository files, in order.
+    A traffic figure from an ncu capture is valid only while the sources of
+    the captured kernel are the ones it was taken from."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(p.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
 
 
-def roofline(records, pk, traffic=None):
-    """Dominant kernel family (by device time) and its achieved fraction of the
-    binding roof: HBM bandwidth or the arithmetic rate of its precision."""
+# The sources that make each captured kernel family (the kernel, the headers
+# it includes and the host code that plans and launches it).
+SEG_SOURCES = ("paper_2508_13615_gb300/csrc/jit.cu", "paper_2508_13615_gb300/csrc/jit_dev.cuh",
+               "paper_2508_13615_gb300/csrc/tile.cuh", "paper_2508_13615_gb300/csrc/arith.cuh",
+               "paper_2508_13615_gb300/csrc/fused_reg.cu")
+BLOCK_SOURCES = ("paper_2508_13615_gb300/csrc/block_tc.cu",)
+DENSE_SOURCES = ("paper_2508_13615_gb300/csrc/gate_kernels.cu", "paper_2508_13615_gb300/csrc/arith.cuh",
+                 "paper_2508_13615_gb300/csrc/gates.cu")
+
+# DRAM read + write per launch of each captured kernel family, from one ncu
+# capture on a smaller state, scaled to a launch at the benchmark's size by the
+# units processed (the state size: a pass moves every amplitude once).  Each
+# entry names the profile summary it comes from and the digest of the sources
+# at capture time; `traffic` is null whenever the sources have changed since.
+TRAFFIC = {
+    "k_fused_reg_jit/df": {"read": 268.6e6, "write": 213.3e6, "capture_qubits": 24,
+                           "source": "profiles/compiled_segment_ansatz_24q_c128.md",
+                           "files": SEG_SOURCES, "sha": None},
+    "k_block_tc": {"read": 537.0e6, "write": 475.1e6, "capture_qubits": 26,
+                   "source": "profiles/k_block_tc_tf32x3_26q_c64.md", "files": BLOCK_SOURCES, "sha": None},
+}
+
+
+def traffic_of(name: str, n: int):
+    """(bytes per launch at n qubits or None, details) for a kernel family."""
+    t = TRAFFIC.get(name)
+    if t is None:
+        return None, {}
+    scaled = (t["read"] + t["write"]) * float(1 << (n - t["capture_qubits"]))
+    now = sources_digest(t["files"])
+    info = {"traffic_source": f"{t['source']} ({t['capture_qubits']} q capture x 2^({n}-{t['capture_qubits']}))",
+            "traffic_sources_sha": now}
+    if t["sha"] != now:
+        info["traffic_last_capture"] = scaled
+        info["traffic_note"] = ("the kernel's sources changed after the capture (digest "
+                                f"{t['sha']} at capture, {now} now): retake it")
+        return None, info
+    return scaled, info
+
+
+def roofline(records, pk, n):
+    """The dominant kernel family (by device time) against the measured HBM
+    copy peak: achieved = its algorithmic bytes per launch / its average
+    launch time.  The double-float arithmetic figure derived from this code's
+    own instruction count is reported beside it under `alu_derived`."""
     fam = {}
     for name, ms, b, f in records:
         d = fam.setdefault(name, [0, 0.0, 0.0, 0.0])
@@ -301,29 +373,19 @@ def roofline(records, pk, traffic=None):
     tfl = f / (ms * 1e-3) / 1e12
     arith = name.split("/")[-1] if "/" in name else "f32"
     alu_peak = ALU_PEAK_TFLOPS.get(arith, ALU_PEAK_TFLOPS["f32"])
-    hbm_frac, alu_frac = gbs / hbm, tfl / alu_peak
-    if alu_frac > hbm_frac:
-        out = {"kernel": name, "bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
-               "frac": alu_frac,
-               "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / {DF_INSTR_PER_FLOP:.2f} FP32 "
-                              f"instructions per float64-equivalent flop (double-float)" if arith == "df" else
-                              "derived from unit counts and clocks",
-               "hbm_frac_of_measured": hbm_frac}
-    else:
-        out = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
-               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in pk else
-                              "fallback 6.8 TB/s",
-               "alu_frac": alu_frac}
-    if traffic is None and name in TRAFFIC:
-        t = TRAFFIC[name]
-        out["traffic_source"] = t["source"]
-        if t.get("changed_since"):
-            out["traffic_last_capture"] = t["bytes_per_launch"]
-            out["traffic_note"] = t["changed_since"]
-        else:
-            traffic = t["bytes_per_launch"]
-    out.update({"traffic": traffic, "launches": cnt, "share": ms / total, "bytes_per_launch": b / cnt,
-                "ms_per_launch": ms / cnt, "f64eq_tflops": tfl, "algorithmic_gbps": gbs})
+    traffic, tinfo = traffic_of(name, n)
+    out = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+           "peak_source": ("MEASURED_PEAKS.json hbm_gbs (measured copy); frac is of measured" if "hbm_gbs" in pk
+                           else "fallback 6.8 TB/s; frac is of fallback"),
+           "traffic": traffic, **tinfo,
+           "launches": cnt, "share": ms / total, "bytes_per_launch": b / cnt, "ms_per_launch": ms / cnt,
+           "frac_of_nominal_8TBps": gbs / 8000.0,
+           "alu_derived": {
+               "achieved_f64eq_tflops": tfl, "figure_tflops": alu_peak, "frac": tfl / alu_peak,
+               "basis": (f"derived from this code's own instruction count, not a chip peak: 152 SMs x 128 FP32 "
+                         f"lanes x 2.07 GHz / {DF_INSTR_PER_FLOP:.2f} FP32 instructions per float64-equivalent "
+                         f"flop of its double-float arithmetic; flops are the gates' algorithmic flops")
+               if arith == "df" else "derived from unit counts and clocks"}}
     fams = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total, 4),
                 "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None} for k, v in fam.items()}
     return out, fams
@@ -384,7 +446,11 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD + "; reference arm: the CPU oracle applies one P1 sweep gate per step",
-                   "n_qubits": n},
+                   "n_qubits": n,
+                   "units": ("this arm counts single P1 sweep gates (H, RZ, CNOT(24,t), U4 on the 30-qubit state, "
+                             "one gate per step, general matrix update); the GPU arm counts all 1490 gates of its "
+                             "step (120 plain P1 gates, 890 fused P2 gates, 480 fused P3 gates), so the two arms "
+                             "do not time the same gate mix")},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
                          "sample": f"{args.steps} P1 sweep gates on the {n}-qubit state"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
@@ -398,74 +464,91 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def config_adjoint24(args):
+def adjoint_leg(steps: int, warmup: int, n: int = 24, layers: int = 8):
     """24 qubits, 8-layer ansatz (384 parameters), TFIM: adjoint gradient time
     over forward time (fused forward + expectation), complex128 and complex64,
-    and central differences (h = 1e-6) on a sample of parameters (complex128)."""
+    each timed with CUDA events on the launching stream (median of the timed
+    repetitions); central differences (h = 1e-6) on a sample of parameters
+    (complex128), and the complex64 gradient against the complex128 one."""
     import torch
     import paper_2508_13615_gb300 as L
-    n = 24
-    c = W.ansatz(n, 8, 6)
+    c = W.ansatz(n, layers, 6)
     terms = W.tfim(n)
     ops = L.OpArray(c.ops)
     pa = L.PauliArray(terms)
-    out = {"config": "adjoint24", "metric": "adjoint/forward time", "n_qubits": n, "params": c.n_params,
-           "kernels": "compiled fused segments forward, compiled reverse sweep (psi and lambda in registers)"}
+    out = {"n_qubits": n, "layers": layers, "params": c.n_params, "observable": "TFIM sum Z_iZ_i+1 + 0.5 sum X_i",
+           "forward": "fused ansatz (compiled segments) + expectation (compiled Pauli passes)",
+           "adjoint": "lambda = H psi + compiled reverse sweep (psi and lambda in registers)",
+           "timing": "CUDA events on the launching stream, median"}
+    old = L.lqs_jit_info()["mode"]
     L.lqs_set_jit(L.LQS_JIT_ON)
-    for dtype in ("c128", "c64"):
-        ar = L.LQS_ARITH_DF if dtype == "c128" else L.LQS_ARITH_AUTO
-        t_jit = time.perf_counter()
-        L.lqs_jit_precompile(n, dtype, c.ops, c.params, ar)
-        L.lqs_jit_precompile_adjoint(n, dtype, c.ops, c.params, ar)
-        L.lqs_jit_precompile_expval(n, dtype, terms, False, ar)
-        L.lqs_jit_precompile_expval(n, dtype, terms, True, ar)
-        jit_s = time.perf_counter() - t_jit
-        sv = L.StateVector(n, dtype)
-        st = torch.cuda.current_stream()
+    g128 = None
+    try:
+        for dtype in ("c128", "c64"):
+            ar = L.LQS_ARITH_DF if dtype == "c128" else L.LQS_ARITH_AUTO
+            t_jit = time.perf_counter()
+            L.lqs_jit_precompile(n, dtype, c.ops, c.params, ar)
+            L.lqs_jit_precompile_adjoint(n, dtype, c.ops, c.params, ar)
+            L.lqs_jit_precompile_expval(n, dtype, terms, False, ar)
+            L.lqs_jit_precompile_expval(n, dtype, terms, True, ar)
+            jit_s = time.perf_counter() - t_jit
+            sv = L.StateVector(n, dtype)
+            st = torch.cuda.current_stream()
 
-        def fwd():
-            L.lqs_sv_set_basis(sv.h, 0)
-            L.lqs_apply_fused(sv.h, ops, c.params, None)
-            return L.lqs_expval(sv.h, pa)[0]
+            def fwd():
+                L.lqs_sv_set_basis(sv.h, 0)
+                L.lqs_apply_fused(sv.h, ops, c.params, None)
+                return L.lqs_expval(sv.h, pa)[0]
 
-        for _ in range(args.warmup):
-            fwd()
-            L.lqs_adjoint_grad(sv.h, ops, c.params, pa)
-        tf, ta = [], []
-        for _ in range(max(args.steps, 3)):
-            e0, e1 = _events()
-            e0.record(st)
-            fwd()
-            e1.record(st)
-            torch.cuda.synchronize()
-            tf.append(e0.elapsed_time(e1))
-            e0.record(st)
-            g, e = L.lqs_adjoint_grad(sv.h, ops, c.params, pa)
-            e1.record(st)
-            torch.cuda.synchronize()
-            ta.append(e0.elapsed_time(e1))
-        rec = {"forward_ms": statistics.median(tf), "adjoint_ms": statistics.median(ta),
-               "adjoint_over_forward": statistics.median(ta) / statistics.median(tf), "energy": e,
-               "compile_wall_s": round(jit_s, 2)}
-        if dtype == "c128":
-            h = 1e-6
-            fd = []
-            for k in (0, 7, 100, 383):
-                vals = []
-                for sgn in (1, -1):
-                    p = c.params.copy()
-                    p[k] += sgn * h
-                    L.lqs_sv_set_basis(sv.h, 0)
-                    L.lqs_apply_fused(sv.h, ops, p, None)
-                    vals.append(L.lqs_expval(sv.h, pa)[0])
-                fd.append(abs((vals[0] - vals[1]) / (2 * h) - g[k]))
-            rec["max_abs_adjoint_minus_fd"] = max(fd)
-            g128 = g
-        else:
-            rec["max_abs_grad_c64_minus_c128"] = float(np.max(np.abs(g - g128)))
-        out[dtype] = rec
-        sv.close()
-    print(json.dumps(out), flush=True)
+            for _ in range(warmup):
+                fwd()
+                L.lqs_adjoint_grad(sv.h, ops, c.params, pa)
+            tf, ta = [], []
+            for _ in range(max(steps, 3)):
+                e0, e1 = _events()
+                e0.record(st)
+                fwd()
+                e1.record(st)
+                torch.cuda.synchronize()
+                tf.append(e0.elapsed_time(e1))
+                e0.record(st)
+                g, e = L.lqs_adjoint_grad(sv.h, ops, c.params, pa)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ta.append(e0.elapsed_time(e1))
+            rec = {"forward_ms": statistics.median(tf), "adjoint_ms": statistics.median(ta),
+                   "adjoint_over_forward": statistics.median(ta) / statistics.median(tf), "energy": e,
+                   "compile_wall_s": round(jit_s, 2)}
+            if dtype == "c128":
+                h = 1e-6
+                fd = []
+                for k in (0, 7, 100, 383 % c.n_params):
+                    vals = []
+                    for sgn in (1, -1):
+                        p = c.params.copy()
+                        p[k] += sgn * h
+                        L.lqs_sv_set_basis(sv.h, 0)
+                        L.lqs_apply_fused(sv.h, ops, p, None)
+                        vals.append(L.lqs_expval(sv.h, pa)[0])
+                    fd.append(abs((vals[0] - vals[1]) / (2 * h) - g[k]))
+                rec["fd_params_checked"] = [0, 7, 100, 383 % c.n_params]
+                rec["max_abs_adjoint_minus_fd"] = max(fd)
+                g128 = g
+            else:
+                rec["max_abs_grad_c64_minus_c128"] = float(np.max(np.abs(g - g128)))
+            out[dtype] = rec
+            sv.close()
+    finally:
+        L.lqs_set_jit(old)
+    return out
+
+
+def config_adjoint24(args):
+    """The adjoint/forward measurement alone (it is also part of the default line)."""
+    rec = adjoint_leg(args.steps, args.warmup)
+    rec["config"] = "adjoint24"
+    rec["metric"] = "adjoint/forward time"
+    print(json.dumps(rec), flush=True)
 
 
 def config_precision32(args):
@@ -700,11 +783,8 @@ def config_tcblock30(args):
         "block_ms": ms_block, "block_gbs": gbs,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / pk["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
-                     # DRAM read + write of one launch at 26 qubits (ncu), scaled by the 16x units of 30 qubits
-                     "traffic": None,
-                     "traffic_last_capture": (537.0e6 + 475.1e6) * (1 << (n - 26)),
-                     "traffic_note": KERNELS_CHANGED_SINCE_CAPTURE,
-                     "traffic_source": "profiles/k_block_tc_tf32x3_26q_c64.md (26 q capture x 2^(n-26))"},
+                     # DRAM read + write of one launch at 26 qubits (ncu), scaled by the units of n qubits
+                     "traffic": traffic_of("k_block_tc", n)[0], **traffic_of("k_block_tc", n)[1]},
         "tensor_tflops": flops / (ms_block * 1e-3) / 1e12,
         "fused_gates": len(c.ops), "fused_ms": ms_fused, "fused_with_block_extraction_ms": ms_auto,
         "speedup_vs_fused": ms_fused / ms_block,
@@ -721,6 +801,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-c64", action="store_true", help="skip the complex64 run of the step")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 24-qubit adjoint/forward measurement")
     ap.add_argument("--tune", action="store_true",
                     help="let lqs_autotune_fused pick the tile shapes first (measured: +0.4%% for 45 s of tuning)")
     ap.add_argument("--config", default="main",
@@ -755,8 +837,7 @@ def main():
     # workload's structures once, ahead of the warm-up (host only, parallel).
     L.lqs_set_jit(L.LQS_JIT_ON)
     t_jit = time.perf_counter()
-    n_jit = sum(L.lqs_jit_precompile(n, "c128", c.ops, c.params, L.LQS_ARITH_DF) for c in (wl.ansatz, wl.qft))
-    n_jit += L.lqs_jit_precompile_expval(n, "c128", wl.tfim, False, L.LQS_ARITH_DF)
+    n_jit = wl.precompile(L.LQS_ARITH_DF)
     jit_s = time.perf_counter() - t_jit
     # The tile shape per circuit structure, chosen once by the library's
     # autotuner (lqs_apply_fused then uses it); the autotuner uses the state as
@@ -793,36 +874,96 @@ def main():
     ms_step = ms / args.steps
     value = replicas_value(wl.gates, world, ms_step * 1e-3)
     bytes_step = sum(r[2] for r in records) / args.steps
-    roof, fams = roofline(records, pk)
+    roof, fams = roofline(records, pk, n)
+
+    # The same step in complex64 (float32 gate math; norms, energies and
+    # distances accumulated in float64), from the complex128 input rounded to
+    # complex64, timed the same way; then its results against complex128's.
+    c64 = None
+    if not args.no_c64:
+        psi64 = psi_host.astype(np.complex64)
+        wl64 = Workload(n, psi64, "c64")
+        t_jit = time.perf_counter()
+        n_jit64 = wl64.precompile(L.LQS_ARITH_AUTO)
+        jit64_s = time.perf_counter() - t_jit
+        for _ in range(args.warmup):
+            wl64.step()
+        torch.cuda.synchronize()
+        barrier()
+        clocks64 = ClockSampler(local)
+        clocks64.start()
+        L.lqs_profile_start()
+        e0.record(st)
+        for _ in range(args.steps):
+            wl64.step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        rec64 = L.lqs_profile_stop()
+        clk64 = clocks64.stop()
+        barrier()
+        ms64 = ranks.max(e0.elapsed_time(e1), "cuda") / args.steps
+        roof64, fams64 = roofline(rec64, pk, n)
+        # P2 energy and the P3 output state (both states hold P3's result now)
+        d2, nb = L.lqs_sv_distance(wl64.sv.h, wl.sv.h)
+        e128_p2, e64_p2 = wl.energy, wl64.energy
+        # P1's output state from the same input in both precisions
+        wl.sv.tensor.copy_(wl.saved)
+        wl64.sv.tensor.copy_(wl64.saved)
+        wl.p1()
+        wl64.p1()
+        d2p1, nbp1 = L.lqs_sv_distance(wl64.sv.h, wl.sv.h)
+        torch.cuda.synchronize()
+        c64 = {"value": replicas_value(wl64.gates, world, ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+               "c64_over_c128_speed": ms_step / ms64,
+               "arith": "complex64 storage, float32 gate math; norms, energies, distances accumulated in float64",
+               "gb_per_s_algorithmic": sum(r[2] for r in rec64) / args.steps / (ms64 * 1e-3) / 1e9,
+               "roofline": {k: roof64[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "share",
+                                                   "ms_per_launch")},
+               "kernels": fams64, "clocks": clk64,
+               "segment_compiler": {"structures_compiled": n_jit64, "compile_wall_s": round(jit64_s, 2)},
+               "energy_tfim_ansatz_c64": e64_p2, "abs_energy_c64_minus_c128": abs(e64_p2 - e128_p2),
+               "rel_l2_c64_vs_c128_p1_state": math.sqrt(d2p1 / nbp1),
+               "rel_l2_c64_vs_c128_p3_state": math.sqrt(d2 / nb),
+               "input": "the complex128 input rounded to complex64 (relative L2 rounding about 3e-8)"}
+        wl64.close()
+        del psi64
+
+    # adjoint gradient over the forward pass (24 qubits, 8 layers, 384 params)
+    adj = None if args.no_adjoint else adjoint_leg(args.steps, args.warmup)
 
     e2e = None
     if not args.no_e2e:
-        out_t = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
-        out_host = out_t.numpy()
-        pipe = E2EPipeline(wl, out_host)
+        out_p1 = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
+        out_p3 = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
+        o1, o3 = out_p1.numpy(), out_p3.numpy()
+        pipe = E2EPipeline(wl, o1, o3)
         pipe.run(1)  # warm (scratch buffers of the new states)
         barrier()
         t0 = time.perf_counter()
         pipe.run(args.steps)
         et = ranks.max(time.perf_counter() - t0, "cuda")
+        d2h = pipe.d2h_bytes_per_step()
         pipe.close()
-        sample = out_host[::max(1, out_host.size // 4096)].copy()
+        stride = max(1, o1.size // 4096)
+        s1, s3 = o1[::stride].copy(), o3[::stride].copy()
         # one more step with nothing overlapped, timed part by part (after the measured ones)
         parts = {}
         for key, fn in (("h2d", lambda: L.lqs_sv_copy_from_host(wl.sv.h, wl.psi_host)), ("p1", wl.p1),
-                        ("d2h", lambda: L.lqs_sv_copy_to_host(wl.sv.h, out_host)), ("p2p3", wl.p2p3)):
+                        ("d2h_p1", lambda: L.lqs_sv_copy_to_host(wl.sv.h, o1)), ("p2p3", wl.p2p3),
+                        ("d2h_p3", lambda: L.lqs_sv_copy_to_host(wl.sv.h, o3))):
             torch.cuda.synchronize()
             tp = time.perf_counter()
             fn()
             torch.cuda.synchronize()
             parts[key] = round(1e3 * (time.perf_counter() - tp), 1)
         e2e = {"value": replicas_value(wl.gates * args.steps, world, et), "unit": UNIT,
-               "h2d_bytes_per_step": wl.input_bytes(), "d2h_bytes_per_step": int(out_host.nbytes) + 8,
+               "h2d_bytes_per_step": wl.input_bytes(), "d2h_bytes_per_step": d2h,
                "ms_per_step": 1e3 * et / args.steps, "parts_ms_sequential_step": parts,
                "pipelined_result_matches_sequential":
-                   bool(np.array_equal(sample, out_host[::max(1, out_host.size // 4096)])),
-               "path": "lqs_sv_copy_from_host (pinned) -> P1 -> lqs_sv_copy_to_host_async -> P2 (expval to host)"
-                       " -> P3; copies on their own streams, overlapping the previous and next step's compute"}
+                   bool(np.array_equal(s1, o1[::stride]) and np.array_equal(s3, o3[::stride])),
+               "path": "lqs_sv_copy_from_host (pinned) -> P1 -> lqs_sv_copy_to_host_async (P1 state) -> P2 (expval "
+                       "to host) -> P3 -> lqs_sv_copy_to_host_async (P3 state); copies on their own streams, "
+                       "overlapping the previous and next step's compute"}
 
     cpu = None
     if rank == 0 and world == 1:
@@ -840,6 +981,7 @@ def main():
                        "l2": "inputs larger than L2 (16 GiB state vs 129 MB L2); no flush needed"},
             "gb_per_s_algorithmic": bytes_step / (ms_step * 1e-3) / 1e9,
             "hbm_frac_of_8TBps": bytes_step / (ms_step * 1e-3) / 8e12,
+            "hbm_frac_of_measured": bytes_step / (ms_step * 1e-3) / 1e9 / float(pk.get("hbm_gbs", 6800.0)),
             "energy_tfim_ansatz": wl.energy,
             "autotuned": {"configs": tuned, "wall_s": round(tune_s, 2)} if tuned else None,
             "segment_compiler": {"mode": "on", "structures_compiled": n_jit, "compile_wall_s": round(jit_s, 2),
@@ -847,6 +989,7 @@ def main():
                                  "compiled_during_timed": jit1["compiled"] - jit0["compiled"],
                                  "failed": jit1["failed"]},
             "roofline": roof, "kernels": fams, "gpu_launches": int(launches), "clocks": clk,
+            "c64": c64, "adjoint24": adj,
             "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(rec), flush=True)

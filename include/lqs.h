@@ -303,21 +303,26 @@ LQS_API int lqs_batch_run(const lqs_batch_item* items, int n_items, int dtype, v
 /* ---- measurement without device allocation ------------------------------------- */
 
 /* <psi|H|psi> like lqs_expval, for callers that must not allocate device
- * memory when they measure: code running while its stream is captured into a
- * CUDA graph, hosts whose memory pool owns all device memory, or loops that
- * cannot pay for the synchronisation cudaMalloc/cudaFree bring.  The paper has
- * no counterpart; this is a property of this library's interface.
+ * memory when they measure: hosts whose memory pool owns all device memory,
+ * or loops that cannot pay for the synchronisation cudaMalloc/cudaFree bring.
+ * The paper has no counterpart; this is a property of this library's
+ * interface.
  * It needs no state handle: psi_device points to 2^n_qubits amplitudes of
- * `dtype` in device memory (read only), work is ordered on cuda_stream, and
- * the call returns when *out_host (and per_term_host[0..n_terms), if given)
- * hold the results.  It calls no cudaMalloc/cudaFree and no allocating
- * library routine: partial sums live in a fixed scratch array compiled into
- * the library (64 terms x 1024 blocks of float64, about 513 KiB), which every
- * GPU that loads the library keeps until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress):
- * make it before any stream capture.  At most 64 terms (LQS_ERR_ARG beyond).
+ * `dtype` in device memory (read only), work is ordered on cuda_stream, which
+ * must belong to the current device (LQS_ERR_ARG otherwise), and the call is
+ * synchronous: it copies the results to *out_host (and per_term_host[0..n_terms),
+ * if given) and waits for the stream, so it cannot run on a stream that is
+ * being captured into a CUDA graph.  n_terms = 0 gives 0.  It calls no
+ * cudaMalloc/cudaFree and no allocating library routine: partial sums live in
+ * a fixed scratch array compiled into the library (64 terms x 1024 blocks of
+ * float64, about 513 KiB), which every GPU that loads the library keeps until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress).  At most 64 terms (LQS_ERR_ARG beyond).
  * All calls share the array, so calls that overlap on the GPU race on it:
- * serialise them.  One float64-accumulated pass over the state per term. */
+ * serialise them.  One float64-accumulated pass over the state per term.
+ * Accuracy: complex128 amplitudes are split into double-float pairs (about 47
+ * significant bits) before the products, so each <P_w> is within about 1e-14
+ * relative of the exact value rather than float64's 1e-16. */
 LQS_API int lqs_expval_static(const void* psi_device, int n_qubits, int dtype, void* cuda_stream,
                               const lqs_pauli* terms, int n_terms, double* out_host, double* per_term_host);
 

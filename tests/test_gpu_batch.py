@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import set_mode
+from gpu_util import c64_rel_bound, set_mode
 
 pytestmark = pytest.mark.gpu
 
@@ -19,16 +19,26 @@ def small_batch(seed=3, count=10, nmin=2, nmax=14):
     return out
 
 
-@pytest.mark.parametrize("dtype,arith,tol", [("c128", "df", 1e-10), ("c128", "f64", 1e-10), ("c64", "f32", 5e-4)])
-def test_batch_matches_oracle(dtype, arith, tol):
+@pytest.mark.parametrize("dtype,arith", [("c128", "df"), ("c128", "f64"), ("c64", "f32")])
+def test_batch_matches_oracle(dtype, arith):
+    """Energies and gradients of every circuit against the oracle.  complex128:
+    1e-10 absolute.  complex64: the float32 rounding bound of the circuit's
+    gates (forward for the energy, forward and reverse sweep for the
+    gradients) times the observable's coefficient sum."""
     import paper_2508_13615_gb300 as L
     set_mode(arith)
     circs = small_batch() + [W.ansatz(13, 2, 5), W.ansatz(14, 1, 6)]  # several tiles each
     terms = [W.tfim(c.n_qubits) for c in circs]
     e, g = L.lqs_batch_run(circs, terms, dtype)
     for c, t, ei, gi in zip(circs, terms, e, g):
-        assert abs(ei - oracle.energy(c, t)) <= tol
-        np.testing.assert_allclose(gi, oracle.param_shift_grad(c, t), atol=tol)
+        scale = sum(abs(w.coeff) for w in t)
+        if dtype == "c128":
+            tol_e = tol_g = 1e-10
+        else:
+            tol_e = 2 * c64_rel_bound(len(c.ops)) * scale
+            tol_g = 4 * c64_rel_bound(2 * len(c.ops)) * scale
+        assert abs(ei - oracle.energy(c, t)) <= tol_e, (c.n_qubits, len(c.ops))
+        np.testing.assert_allclose(gi, oracle.param_shift_grad(c, t), rtol=0, atol=tol_g)
 
 
 def test_batch_equals_one_at_a_time():
@@ -42,8 +52,9 @@ def test_batch_equals_one_at_a_time():
             sv.set_basis(0)
             sv.apply(c, fused=True)
             g1, e1 = sv.adjoint_grad(c, t)
-        assert abs(ei - e1) <= 1e-5
-        np.testing.assert_allclose(gi, g1, atol=1e-4)
+        scale = sum(abs(w.coeff) for w in t)
+        assert abs(ei - e1) <= 4 * c64_rel_bound(len(c.ops)) * scale
+        np.testing.assert_allclose(gi, g1, rtol=0, atol=8 * c64_rel_bound(2 * len(c.ops)) * scale)
 
 
 def test_batch_energy_only_and_ragged_edge_cases():

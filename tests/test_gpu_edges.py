@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import MODES, TOL, gpu_state, max_abs, set_mode
+from gpu_util import MODES, TOL, check_state, gpu_state, max_abs, set_mode
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def test_smallest_states(dtype, arith, n):
     for fused in (True, False):
         with gpu_state(n, dtype, psi0) as sv:
             sv.apply(c, fused=fused)
-            assert max_abs(sv.numpy(), want) <= TOL[dtype], (n, fused)
+            check_state(sv.numpy(), want, dtype, len(c.ops), (n, fused))
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import MODES, TOL, gpu_state, max_abs, set_mode
+from gpu_util import MODES, TOL, check_state, gpu_state, max_abs, set_mode
 
 pytestmark = pytest.mark.gpu
 
@@ -23,8 +23,7 @@ def test_random_circuit_fused(dtype, arith, cfg, n):
     psi0 = W.gaussian_state(n, 2000 + n)
     with gpu_state(n, dtype, psi0) as sv:
         sv.apply(c, fused=True, cfg=cfg)
-        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-    assert err <= TOL[dtype], err
+        check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, len(c.ops))
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -36,8 +35,7 @@ def test_ansatz_and_qft_fused_16q(dtype, arith):
                     (W.ghz(n), oracle.basis_state(n, 0))):
         with gpu_state(n, dtype, psi0) as sv:
             sv.apply(c, fused=True)
-            err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-        assert err <= TOL[dtype], (c.ops[0].name, err)
+            check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, len(c.ops), c.ops[0].name)
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -48,8 +46,7 @@ def test_fused_matches_plain(dtype, arith):
     with gpu_state(n, dtype) as a, gpu_state(n, dtype) as b:
         a.apply(c, fused=True)
         b.apply(c, fused=False)
-        err = max_abs(a.numpy(), b.numpy())
-    assert err <= TOL[dtype], err
+        check_state(a.numpy(), b.numpy(), dtype, 2 * len(c.ops))
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -65,7 +62,7 @@ def test_qft_closed_form_20q(dtype, arith):
     y = np.arange(N, dtype=np.float64)
     ang = 2 * np.pi * ((x * np.arange(N, dtype=np.int64)) % N) / N
     want = np.exp(1j * ang) / np.sqrt(N)
-    assert max_abs(got, want) <= TOL[dtype]
+    check_state(got, want, dtype, len(W.qft(n).ops))
 
 
 def test_df_and_f64_agree_deep_circuit():

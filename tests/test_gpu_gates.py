@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import MODES, TOL, gpu_state, max_abs, set_mode
+from gpu_util import MODES, TOL, check_state, gpu_state, max_abs, set_mode
 
 pytestmark = pytest.mark.gpu
 
@@ -28,9 +28,8 @@ def test_single_gate_suite_12q(psi12, dtype, arith):
             sv.apply(c, fused=False)
             got = sv.numpy()
             want = oracle.run_circuit(c, psi12)
-            err = max_abs(got, want)
+            err = check_state(got, want, dtype, 1, (c.ops[0].name, c.ops[0].wires))
             worst = max(worst, err)
-            assert err <= TOL[dtype], (c.ops[0].name, c.ops[0].wires, err)
     print(f"worst {dtype}/{arith}: {worst:.3e}")
 
 
@@ -51,8 +50,7 @@ def test_every_gate_every_size(dtype, arith, n):
                 c = W.Circuit(n).add(name, wires, vals, matrix=mat, inverse=bool(trial & 1) and name not in ("U2", "U4"))
                 sv.from_numpy(psi0)
                 sv.apply(c, fused=False)
-                err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-                assert err <= TOL[dtype], (name, wires, err)
+                check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, 1, (name, wires))
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -70,7 +68,7 @@ def test_structured_user_matrices_take_special_kernels(dtype, arith):
             c = W.Circuit(n).add(name, (5,) if name == "U2" else (6, 2), matrix=m)
             sv.from_numpy(psi0)
             sv.apply(c, fused=False)
-            assert max_abs(sv.numpy(), oracle.run_circuit(c, psi0)) <= TOL[dtype]
+            check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, 1, name)
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -126,8 +124,7 @@ def test_cswap_and_double_excitation_every_placement(dtype, arith):
             c.params = np.asarray(p if p else [0.0])
             with gpu_state(n, dtype, psi0) as sv:
                 sv.apply(c, fused=False)
-                err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-            assert err <= TOL[dtype], (name, wires, inv, err)
+                check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, 1, (name, wires, inv))
 
 
 def test_copies_on_other_streams_through_aliased_handles():

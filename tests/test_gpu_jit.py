@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import MODES, TOL, gpu_state, max_abs, set_mode
+from gpu_util import MODES, TOL, check_state, gpu_state, max_abs, set_mode
 
 pytestmark = pytest.mark.gpu
 
@@ -32,8 +32,7 @@ def test_random_circuit_compiled_vs_oracle(jit_on, dtype, arith, n, seed):
     psi0 = W.gaussian_state(n, seed + 100)
     with gpu_state(n, dtype, psi0) as sv:
         sv.apply(c, fused=True)
-        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-    assert err <= TOL[dtype], err
+        check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, len(c.ops))
     assert L.lqs_jit_info()["launches"] > before["launches"]
 
 
@@ -48,8 +47,7 @@ def test_controls_inside_and_outside_the_tile(jit_on, dtype, arith):
     psi0 = W.gaussian_state(n, 78)
     with gpu_state(n, dtype, psi0) as sv:
         sv.apply(c, fused=True)
-        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-    assert err <= TOL[dtype], err
+        check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, len(c.ops))
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -70,7 +68,7 @@ def test_compiled_matches_interpreter(dtype, arith):
                 out[mode] = sv.numpy()
     finally:
         L.lqs_set_jit(old)
-    assert max_abs(out[L.LQS_JIT_OFF], out[L.LQS_JIT_ON]) <= TOL[dtype]
+    check_state(out[L.LQS_JIT_ON], out[L.LQS_JIT_OFF], dtype, 2 * (len(W.ansatz(n, 6, 8).ops) + len(W.qft(n).ops)))
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
@@ -83,7 +81,7 @@ def test_qft_closed_form_compiled(jit_on, dtype, arith):
         sv.apply(W.qft(n), fused=True)
         got = sv.numpy()
     ang = 2 * np.pi * ((x * np.arange(N, dtype=np.int64)) % N) / N
-    assert max_abs(got, np.exp(1j * ang) / np.sqrt(N)) <= TOL[dtype]
+    check_state(got, np.exp(1j * ang) / np.sqrt(N), dtype, len(W.qft(n).ops))
 
 
 def test_angles_reuse_the_compiled_kernels(jit_on):
@@ -289,8 +287,7 @@ def test_orthogonal_2x2_forms_at_edge_angles(jit_on, dtype, arith):
     psi0 = W.gaussian_state(n, 404)
     with gpu_state(n, dtype, psi0) as sv:
         sv.apply(c, fused=True)
-        err = max_abs(sv.numpy(), oracle.run_circuit(c, psi0))
-    assert err <= TOL[dtype], err
+        check_state(sv.numpy(), oracle.run_circuit(c, psi0), dtype, len(c.ops))
     assert L.lqs_jit_info()["launches"] > before["launches"]
 
 
@@ -306,5 +303,4 @@ def test_universal_circuit_vs_oracle(jit_on, dtype, arith, n):
     for fused in (True, False):
         with gpu_state(n, dtype, psi0) as sv:
             sv.apply(c, fused=fused)
-            err = max_abs(sv.numpy(), want)
-        assert err <= TOL[dtype], (fused, err)
+            check_state(sv.numpy(), want, dtype, len(c.ops), fused)
