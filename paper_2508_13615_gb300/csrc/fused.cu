@@ -227,6 +227,7 @@ void init_prog(TileProg<A>& P, int n, uint64_t Q, int k, int b) {
   P.nops = 0;
   P.ncoef = 0;
   P.ngrad = 0;
+  P.nfold = 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -417,9 +417,13 @@ struct Ent {
   int group = -1;
 };
 
+// fold_perm (compiled segments only): runs of CNOT / X gates whose targets are
+// tile qubits are not emitted as ops; their affine map is attached to the
+// layout change that follows them (TFold), whose exchange then writes every
+// amplitude to its permuted position.  The interpreter takes no folds.
 template <class A>
 static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Segment& seg, int r,
-                          std::vector<int>* grad_ops = nullptr) {
+                          std::vector<int>* grad_ops = nullptr, bool fold_perm = false) {
   // grad_ops (compiled adjoint): every parametrised op gets a gradient slot
   // in emission order and grad_ops receives the op of each slot; members of
   // merged diagonal runs are emitted as K_GRAD partials just before their run
@@ -479,6 +483,12 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
 
   // 2. layouts and emission
   auto nondiag = [&](const Ent& e) { return e.op >= 0 && !ops[e.op].diagonal(); };
+  // a gate that only moves amplitudes by an affine map of the tile bits: X or
+  // CNOT (at most one control) with its target in the tile
+  auto foldable = [&](const KOp& o) {
+    return fold_perm && !has_grad(o) && o.kind == K_ANTI1 && o.special == 1 && __builtin_popcountll(o.cmask) <= 1 &&
+           lp(o.t0) >= 0;
+  };
   auto choose = [&](size_t i, const std::vector<int>& keep) {
     std::vector<int> slot(r, -1);
     auto has = [&](int q) { return std::find(slot.begin(), slot.end(), q) != slot.end(); };
@@ -500,6 +510,7 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
     for (; j < seq.size(); ++j) {
       if (!nondiag(seq[j])) continue;
       const KOp& o = ops[seq[j].op];
+      if (foldable(o)) continue;  // folded into a layout change: needs no register slot
       if (two_target(o)) break;  // it will need its own exact placement
       put(lp(o.t0));
       if (std::count(slot.begin(), slot.end(), -1) == 0) break;
@@ -564,11 +575,26 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
     for (int m = 0; m < k - r; ++m) p |= (uint64_t)thr[m] << (4 * (r + m));
     return p;
   };
+  // The pending folded run, in storage positions: x -> F x ^ c (TFold).
+  TFold pend{};
+  bool pending = false;
+  auto fold_reset = [&]() {
+    pend = TFold{};
+    for (int p = 0; p < k; ++p) pend.col[p] = (uint16_t)(1u << p);
+    pending = false;
+  };
+  fold_reset();
   auto emit_layout = [&](const std::vector<int>& slot, bool keep) -> int {
     if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;  // the caller splits the segment
     TOp t{};
     t.kind = K_LAYOUT;
     t.gslot = -1;
+    if (pending) {
+      if (P.nfold >= kMaxTileFolds) return LQS_ERR_UNSUPPORTED;
+      P.fold[P.nfold] = pend;
+      t.fold = (int16_t)(++P.nfold);
+      fold_reset();
+    }
     const uint64_t logical = keep && have_prev ? pack_keep(slot) : pack(slot);
     prev_logical = logical;
     have_prev = true;
@@ -588,6 +614,52 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
   for (int m = 0; m < r; ++m) natural[m] = k - r + m;
   std::vector<int> cur = natural;
   LQS_TRY(emit_layout(cur, false));
+  // storage position of local qubit q (after relabelling SWAPs), -1 outside the tile
+  auto pp = [&](int q) -> int {
+    const int l = lp(q);
+    return l < 0 ? -1 : pi[l];
+  };
+  // Composes a foldable gate after the pending map: y -> y ^ y_C e_T for a
+  // control on storage position C, y ^ [outside qubit q] e_T, or y ^ e_T.
+  // False when the map has no room for another outside control.
+  auto fold_in = [&](const KOp& o) -> bool {
+    const uint16_t tb = (uint16_t)(1u << pp(o.t0));
+    if (!o.cmask) {
+      pend.cst ^= tb;
+    } else {
+      const int q = __builtin_ctzll(o.cmask);
+      const int C = pp(q);
+      if (C >= 0) {
+        for (int p = 0; p < k; ++p)
+          if ((pend.col[p] >> C) & 1u) pend.col[p] ^= tb;
+        if ((pend.cst >> C) & 1u) pend.cst ^= tb;
+        for (int j = 0; j < pend.nout; ++j)
+          if ((pend.omask[j] >> C) & 1u) pend.omask[j] ^= tb;
+      } else {
+        int j = 0;
+        while (j < pend.nout && pend.oq[j] != q) ++j;
+        if (j == pend.nout) {
+          if (pend.nout >= kMaxFoldOut) return false;
+          pend.oq[j] = (uint8_t)q;
+          pend.omask[j] = 0;
+          ++pend.nout;
+        }
+        pend.omask[j] ^= tb;
+      }
+    }
+    pending = true;
+    return true;
+  };
+  // the layout change that applies a pending fold before entry i
+  auto flush_fold = [&](size_t i) -> int {
+    if (!pending) return LQS_OK;
+    std::vector<int> keep(r);  // the qubits now held in registers
+    for (int m = 0; m < r; ++m)
+      for (int l = 0; l < k; ++l)
+        if (pi[l] == cur[m]) keep[m] = l;
+    cur = choose(i, keep);
+    return emit_layout(cur, true);
+  };
   for (size_t i = 0; i < seq.size(); ++i) {
     if (P.nops >= kMaxTileOps) return LQS_ERR_UNSUPPORTED;
     if (seq[i].op >= 0) {
@@ -597,12 +669,14 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
         std::swap(pi[la], pi[lb]);
         continue;
       }
+      // a permutation whose target is not in registers (or that follows one
+      // already folded) joins the pending fold instead of forcing an exchange
+      if (foldable(so)) {
+        const bool in_reg = std::find(cur.begin(), cur.end(), pp(so.t0)) != cur.end();
+        if ((pending || !in_reg) && fold_in(so)) continue;
+      }
     }
-    // storage position of local qubit q (after relabelling SWAPs), -1 outside the tile
-    auto pp = [&](int q) -> int {
-      const int l = lp(q);
-      return l < 0 ? -1 : pi[l];
-    };
+    LQS_TRY(flush_fold(i));
     if (seq[i].group >= 0) {
       const DGroup& g = groups[seq[i].group];
       for (int mi : g.members) {
@@ -705,7 +779,7 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
       t.s1 = o.t1 >= 0 ? (int8_t)(std::find(cur.begin(), cur.end(), pp(o.t1)) - cur.begin()) : (int8_t)-1;
     }
   }
-  if (cur != natural || !is_identity()) LQS_TRY(emit_layout(natural, false));
+  if (cur != natural || !is_identity() || pending) LQS_TRY(emit_layout(natural, false));
   return LQS_OK;
 }
 
@@ -715,7 +789,8 @@ int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, 
   const int r = RLog<R>::r;
   static thread_local TileProg<A> P;
   init_prog(P, sv->n, seg.qmask, k, b);
-  LQS_TRY(build_reg_prog(P, ops, seg, r));
+  const bool fold = jit_enabled_for(sv->n);  // compiled segments fold permutation runs into exchanges
+  LQS_TRY(build_reg_prog(P, ops, seg, r, nullptr, fold));
   double flops = 0.0;
   for (int i : seg.ops) flops += kop_touched_fraction(ops[i]) * kop_flops_per_amp(ops[i]);
   {
@@ -723,6 +798,10 @@ int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, 
     const std::string jname = std::string("k_fused_reg_jit/") + arith_tag(sv->dtype, arith);
     LQS_TRY(jit_launch(P, r, sv, 2.0 * (double)sv->bytes(), flops * (double)sv->N(), jname.c_str(), &launched));
     if (launched) return LQS_OK;
+  }
+  if (P.nfold) {  // the interpreter applies every gate itself: the same segment without folds
+    init_prog(P, sv->n, seg.qmask, k, b);
+    LQS_TRY(build_reg_prog(P, ops, seg, r));
   }
   const size_t smem = 2 * ((size_t)sizeof(typename A::S) << k) + 16;
   static bool attr_done = false;
@@ -749,7 +828,7 @@ static int note_reg_prog_t(int n, const std::vector<KOp>& ops, const Segment& se
   constexpr int R = RegR<A>::R;
   static thread_local TileProg<A> P;
   init_prog(P, n, seg.qmask, k, b);
-  LQS_TRY(build_reg_prog(P, ops, seg, RLog<R>::r));
+  LQS_TRY(build_reg_prog(P, ops, seg, RLog<R>::r, nullptr, true));
   return jit_note(P, RLog<R>::r, n, force, todo);
 }
 
@@ -801,7 +880,7 @@ static int adj_build(int n, const std::vector<KOp>& rev, const Segment& seg, int
                      std::vector<std::unique_ptr<AdjProg<A>>>& out) {
   auto pr = std::make_unique<AdjProg<A>>();
   init_prog(pr->P, n, seg.qmask, k, b);
-  const int rc = build_reg_prog(pr->P, rev, seg, r, &pr->gops);
+  const int rc = build_reg_prog(pr->P, rev, seg, r, &pr->gops, true);
   if (rc == LQS_OK) {
     pr->P.ngrad = (int)pr->gops.size();
     pr->ops = seg.ops;

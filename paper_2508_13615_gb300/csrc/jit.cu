@@ -97,6 +97,7 @@ class SegGen {
   // and ops with a gradient slot (and K_GRAD partials) add Im<lambda|G|psi>.
   SegGen(int k, int b, int r, const char* aname, int amp_bytes, bool adjoint)
       : k_(k), b_(b), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes), adj_(adjoint) {}
+  void set_folds(const TFold* f) { folds_ = f; }
 
   // Returns false (with a reason) for a program this generator does not take.
   bool run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& src, std::string& kname, std::string& why);
@@ -134,6 +135,15 @@ class SegGen {
   std::vector<char> reach(int v, size_t from) const;
   bool exchange_safe(int buf, const std::vector<uint8_t>& wown) const;
   int nu_ = 0;    // forward: orthogonal real 2x2 ops applied in unit-row form (their g's scale the store)
+  const TFold* folds_ = nullptr;  // permutation runs folded into layout changes (TOp::fold)
+  const TFold* wfold_ = nullptr;  // the fold of the exchange being written (owners() maps through it)
+  // F x (the linear part of a fold) on local position bits
+  static uint32_t fold_lin(const TFold& F, uint32_t x) {
+    uint32_t y = 0;
+    for (int p = 0; x; ++p, x >>= 1)
+      if (x & 1u) y ^= F.col[p];
+    return y;
+  }
 
   int nthreads() const { return 1 << (k_ - r_); }
   void flush_pending(bool all);
@@ -175,7 +185,7 @@ class SegGen {
   std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
   std::string barrier_for(uint64_t to, uint32_t* gmask);
   bool emit_op(const TOp& t);
-  XSwz pick_swizzle(const int* wpos, const int* rpos) const;
+  XSwz pick_swizzle(const uint32_t* wv, const uint32_t* rv) const;
   std::string swz_expr(const std::string& j, const XSwz& x) const;
   bool emit_grad(const TOp& t);
   bool emit_grad_block(const TOp* ops, int count);
@@ -280,17 +290,25 @@ std::string SegGen::barrier_for(uint64_t to, uint32_t* gmask) {
 // exchange re-assigns the fold of the higher lane positions when it must
 // (a small backtracking search), writes and reads through that swizzle, and
 // leaves every other exchange on the default.
-XSwz SegGen::pick_swizzle(const int* wpos, const int* rpos) const {
+XSwz SegGen::pick_swizzle(const uint32_t* wv, const uint32_t* rv) const {
+  // wv / rv: the position vectors of the lane bits of the writing and the
+  // reading layout (single positions, or their images under a fold)
   const int nb = sz_ == 16 ? 3 : 4;
   XSwz x;
   if (k_ - r_ < nb) return x;
   auto dflt = [&](int p) { return host_swz(1u << p, sz_) & ((1u << nb) - 1u); };  // bank bits of swz<sz>
   uint32_t g[16];
   for (int p = 0; p < 16; ++p) g[p] = dflt(p);
-  auto full_rank = [&](const int* pos) {
-    uint32_t span = 1u;  // bit v set: vector v is in the span
+  auto bank = [&](uint32_t v) {
+    uint32_t y = 0;
+    for (int p = 0; v; ++p, v >>= 1)
+      if (v & 1u) y ^= g[p];
+    return y;
+  };
+  auto full_rank = [&](const uint32_t* vec) {
+    uint32_t span = 1u;  // bit u set: vector u is in the span
     for (int i = 0; i < nb; ++i) {
-      const uint32_t v = g[pos[i]];
+      const uint32_t v = bank(vec[i]);
       uint32_t next = span;
       for (uint32_t u = 0; u < (1u << nb); ++u)
         if ((span >> u) & 1u) next |= 1u << (u ^ v);
@@ -298,14 +316,14 @@ XSwz SegGen::pick_swizzle(const int* wpos, const int* rpos) const {
     }
     return span == (nb == 3 ? 0xFFu : 0xFFFFu);
   };
-  if (full_rank(wpos) && full_rank(rpos)) return x;
-  std::vector<int> free_pos;  // lane positions above the low bits: their fold can change
-  for (int i = 0; i < nb; ++i) {
-    for (int p : {wpos[i], rpos[i]})
-      if (p >= nb && std::find(free_pos.begin(), free_pos.end(), p) == free_pos.end()) free_pos.push_back(p);
-  }
+  if (full_rank(wv) && full_rank(rv)) return x;
+  std::vector<int> free_pos;  // positions above the low bits met by a lane vector: their fold can change
+  for (int i = 0; i < nb; ++i)
+    for (uint32_t v : {wv[i], rv[i]})
+      for (int p = nb; p < k_; ++p)
+        if (((v >> p) & 1u) && std::find(free_pos.begin(), free_pos.end(), p) == free_pos.end()) free_pos.push_back(p);
   std::function<bool(size_t)> search = [&](size_t i) {
-    if (i == free_pos.size()) return full_rank(wpos) && full_rank(rpos);
+    if (i == free_pos.size()) return full_rank(wv) && full_rank(rv);
     const int p = free_pos[i];
     for (uint32_t v = 1; v < (1u << nb); ++v) {
       g[p] = v;
@@ -314,11 +332,11 @@ XSwz SegGen::pick_swizzle(const int* wpos, const int* rpos) const {
     g[p] = dflt(p);
     return false;
   };
-  if (!search(0)) return x;  // cannot happen for distinct positions; keep the default
+  if (!search(0)) return x;  // no conflict-free fold found; keep the default
   for (int p = nb; p < k_; ++p) {
     const uint32_t d = g[p] ^ dflt(p);
-    for (int b = 0; b < nb; ++b)
-      if ((d >> b) & 1u) x.dm[b] |= 1u << p;
+    for (int bb = 0; bb < nb; ++bb)
+      if ((d >> bb) & 1u) x.dm[bb] |= 1u << p;
   }
   return x;
 }
@@ -339,7 +357,10 @@ std::vector<uint8_t> SegGen::owners(const XSwz& xs) const {
     uint32_t jt = 0;
     for (int m = 0; m < k_ - r_; ++m)
       if ((tid >> m) & 1) jt |= 1u << thr_[m];
-    for (int e = 0; e < R_; ++e) own[host_xswz(jt | je(e), sz_, xs)] = (uint8_t)(tid >> 5);
+    for (int e = 0; e < R_; ++e) {
+      const uint32_t j = jt | je(e);
+      own[host_xswz(wfold_ ? (fold_lin(*wfold_, j) ^ wfold_->cst) : j, sz_, xs)] = (uint8_t)(tid >> 5);
+    }
   }
   return own;
 }
@@ -392,28 +413,53 @@ void SegGen::emit_layout(const TOp& t) {
   // through its own buffer.  The buffers alternate, so one barrier per state
   // suffices: the previous reader of a buffer finished before the
   // intervening exchange's barrier (or the barriers at the top of the tile
-  // loop).
+  // loop).  A folded permutation run (t.fold) moves every amplitude from its
+  // storage position x to F x ^ c on the way: the writes go to the permuted
+  // positions, the reads are those of the new layout.
+  const TFold* F = t.fold && folds_ ? &folds_[t.fold - 1] : nullptr;
   uint32_t old_je[16];
   for (int e = 0; e < R_; ++e) old_je[e] = je(e);
   const int saved_slot[4] = {slot_[0], slot_[1], slot_[2], slot_[3]};
   int saved_thr[16];
   std::copy(thr_, thr_ + 16, saved_thr);
-  // lane positions of the writing and the reading layout
-  int wpos[4], rpos[4];
-  for (int i = 0; i < 4; ++i) wpos[i] = i < k_ - r_ ? thr_[i] : 0;
+  // lane position vectors of the writing (through the fold) and the reading layout
+  uint32_t wv[4], rv[4];
+  for (int i = 0; i < 4; ++i) {
+    const int p = i < k_ - r_ ? thr_[i] : 0;
+    wv[i] = F ? (uint32_t)F->col[p] : 1u << p;
+  }
   for (int i = 0; i < 4; ++i) {
     const int q = r_ + i < k_ ? (int)((t.ecmask >> (4 * (r_ + i))) & 15u) : 0;
-    rpos[i] = q;
+    rv[i] = 1u << q;
   }
-  const XSwz xs = pick_swizzle(wpos, rpos);
+  const XSwz xs = pick_swizzle(wv, rv);
+  // the thread's write index: jt itself, or F jt ^ c (c from the tile's outside bits)
+  std::string wj = "jt";
+  if (F) {
+    wj = fresh("fj");
+    o_ << "    const uint32_t " << wj << " = jt";
+    for (int m = 0; m < k_ - r_; ++m) {
+      const int p = thr_[m];
+      const uint32_t d = (uint32_t)F->col[p] ^ (1u << p);
+      if (d) o_ << " ^ ((0u - ((jt >> " << p << ") & 1u)) & " << hex32(d) << ")";
+    }
+    if (F->cst) o_ << " ^ " << hex32(F->cst);
+    for (int j = 0; j < F->nout; ++j)
+      if (F->omask[j]) o_ << " ^ ((0u - lqs::jit::obit(base, " << (int)F->oq[j] << ")) & " << hex32(F->omask[j]) << ")";
+    o_ << ";\n";
+  }
   std::string jo;
   if (adj_) {
     jo = fresh("jo");
-    o_ << "    const uint32_t " << jo << " = " << swz_expr("jt", xs) << ";\n";
+    o_ << "    const uint32_t " << jo << " = " << swz_expr(wj, xs) << ";\n";
   }
   bool first = true;
-  // who writes and who reads each buffer position in this exchange
+  // who writes and who reads each buffer position in this exchange (with the
+  // fold, for a tile whose outside bits are 0; a folded exchange is fenced by
+  // block barriers, which hold for every tile)
+  wfold_ = F;
   const std::vector<uint8_t> wown = owners(xs);
+  wfold_ = nullptr;
   set_layout(t.ecmask);
   const std::vector<uint8_t> rown = owners(xs);
   std::copy(saved_slot, saved_slot + 4, slot_);
@@ -424,7 +470,10 @@ void SegGen::emit_layout(const TOp& t) {
     xb_ ^= 1;
     std::copy(saved_slot, saved_slot + 4, slot_);  // barrier groups compare with the current layout
     std::copy(saved_thr, saved_thr + 16, thr_);
-    if (!exchange_safe(xi, wown)) {
+    bool unsafe = !exchange_safe(xi, wown);
+    if (F)  // the write positions move with each tile's outside bits: no earlier user of the buffer may be pending
+      for (const XRec& h : xhist_) unsafe = unsafe || h.buf == xi;
+    if (unsafe) {
       // a warp of another group may still use this buffer's positions from
       // an earlier exchange: wait for the whole block first
       o_ << "    __syncthreads();  // earlier users of this buffer are not ordered before these writes\n";
@@ -432,13 +481,21 @@ void SegGen::emit_layout(const TOp& t) {
       xhist_.clear();
     }
     uint32_t gmask = 0;
-    const std::string bar = barrier_for(t.ecmask, &gmask);
+    std::string bar;
+    if (F) {
+      bar = "__syncthreads();";
+      next_bar_ = 1;
+    } else {
+      bar = barrier_for(t.ecmask, &gmask);
+    }
     if (!gmask) xhist_.clear();
     xhist_.push_back(XRec{xi, gmask != 0, wown, rown, gmask});
     if (adj_) o_ << "    { const uint32_t sj = " << jo << ";\n";
-    else o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
-    for (int e = 0; e < R_; ++e)
-      o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_xswz(old_je[e], sz_, xs)) << "], " << V(e) << ");\n";
+    else o_ << "    { const uint32_t sj = " << swz_expr(wj, xs) << ";\n";
+    for (int e = 0; e < R_; ++e) {
+      const uint32_t pos = F ? fold_lin(*F, old_je[e]) : old_je[e];
+      o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_xswz(pos, sz_, xs)) << "], " << V(e) << ");\n";
+    }
     o_ << "    }\n    " << bar << "\n";
     set_layout(t.ecmask);  // validated by the caller
     if (first) o_ << "    jt = " << jt_expr() << ";\n";
@@ -1033,7 +1090,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   // directly and the exchange is skipped.
   int first = 1;
   uint64_t through = ops[0].ecmask, logical = ops[0].e0;
-  if (nops > 1 && ops[1].kind == K_LAYOUT) {
+  if (nops > 1 && ops[1].kind == K_LAYOUT && !ops[1].fold) {
     set_layout(ops[1].ecmask);
     if (smem_read_degree() <= 2) {
       through = ops[1].ecmask;
@@ -1064,7 +1121,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   o_ << "      } }\n";
   for (int i = first; i < nops; ++i) {
     if (ops[i].kind == K_LAYOUT) {
-      if (i == nops - 1) {
+      if (i == nops - 1 && !ops[i].fold) {
         // The closing layout only restores natural order for the store.  Direct
         // stores need no particular order, so when the current layout, mapped
         // from storage positions to the positions they stand for (relabelled
@@ -1126,7 +1183,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   std::ostringstream s;
   s << "// compiled " << (adj_ ? "adjoint" : "fused") << " segment: " << nops << " ops, " << ncoef
     << " coefficients, " << ngrad << " gradient slots\n"
-    << "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
+    << "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\ntypedef unsigned short uint16_t;\n"
        "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n"
     << "#include \"tile.cuh\"\n#include \"jit_dev.cuh\"\n"
     << "typedef " << aname_ << " A;\n"
@@ -1417,6 +1474,8 @@ std::string struct_key(const TileProg<A>& P, int r, bool adjoint, const char* an
     put(&t.ecmask, 8);
     put(&t.e0, 8);
     put(&t.e1, 8);
+    put(&t.fold, 2);
+    if (t.kind == K_LAYOUT && t.fold > 0 && t.fold <= P.nfold) put(&P.fold[t.fold - 1], sizeof(TFold));
   }
   return k;
 }
@@ -1453,6 +1512,7 @@ template <> struct JitTypeName<ArDF> { static constexpr const char* s = "lqs::Ar
 template <class A>
 int jit_source(const TileProg<A>& P, int r, std::string& src, std::string& name, std::string& why, bool adjoint) {
   SegGen g(P.g.k, P.g.b, r, JitTypeName<A>::s, A::kAmpBytes, adjoint);
+  g.set_folds(P.fold);
   return g.run(P.op, P.nops, P.ncoef, adjoint ? P.ngrad : 0, src, name, why) ? LQS_OK : LQS_ERR_UNSUPPORTED;
 }
 

@@ -210,6 +210,10 @@ __device__ __forceinline__ uint32_t swz(uint32_t j) {
   return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
 }
 
+// Bit q of a tile's base index (an outside qubit's value on that tile), as
+// the 0 / 1 that selects a folded permutation's outside-controlled flips.
+__device__ __forceinline__ uint32_t obit(uint64_t base, int q) { return (uint32_t)(base >> q) & 1u; }
+
 // Bank bits an exchange's swizzle changes relative to swz: bit b is the
 // parity of the position bits in m_b (the masks are literal constants, so
 // unused ones vanish at compile time).

@@ -268,7 +268,7 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
   const bool two_in = lam && !fresh;
   std::ostringstream s;
   s << "// compiled Pauli pass: " << nw << " words, mode " << mode << "\n"
-    << "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
+    << "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\ntypedef unsigned short uint16_t;\n"
        "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n"
     << "#include \"tile.cuh\"\n#include \"jit_dev.cuh\"\n"
     << "typedef " << aname << " A;\n"

@@ -45,7 +45,25 @@ struct TOp {
   uint64_t e0, e1;         // diagonal ops: target bits outside the tile
   int16_t gslot;           // adjoint: gradient slot (-1 none)
   int8_t s0, s1;           // register-tile kernel: register slots of the targets
-  int16_t pad[2];
+  int16_t fold;            // layout changes: 1 + index of the permutation folded into it (0: none)
+  int16_t pad;
+};
+
+// A run of CNOT / X gates whose targets are tile qubits, folded into the layout
+// exchange that follows it.  Such gates only move amplitudes: each maps local
+// index bits x to x ^ x_c e_t (or x ^ e_t, or x ^ [outside bit q] e_t), so a
+// run of them is an affine map x -> F x ^ c over GF(2).  The exchange writes the
+// amplitude at storage position x to F x ^ c instead of x, which applies the
+// whole run for the cost of the exchange it shares.  col[p] = F e_p; c = cst
+// ^ the omask[j] of every outside qubit oq[j] that is 1 on this tile.
+constexpr int kMaxFoldOut = 6;
+constexpr int kMaxTileFolds = 24;
+struct TFold {
+  uint16_t col[kMaxTileBits];
+  uint16_t cst;
+  uint8_t nout, pad;
+  uint8_t oq[kMaxFoldOut];
+  uint16_t omask[kMaxFoldOut];
 };
 
 template <class A>
@@ -54,8 +72,10 @@ struct TileProg {
   int nops;
   int ncoef;               // coefficients used in the pool
   int ngrad;               // adjoint: number of gradient slots
+  int nfold;               // permutation runs folded into layout changes (compiled segments only)
   TOp op[kMaxTileOps];
   typename A::C coef[kMaxTileCoef];
+  TFold fold[kMaxTileFolds];
 };
 
 // ---------------------------------------------------------------------------

@@ -125,6 +125,15 @@ def _bank_model(src):
     def pfold(j, *m):
         return sum((bin(j & mb).count("1") & 1) << b for b, mb in enumerate(m))
 
+    def obit(base, q):
+        return (base >> q) & 1
+
+    def py(expr):
+        expr = re.sub(r"(0x[0-9a-f]+)u", r"\1", expr)
+        expr = re.sub(r"\b(\d+)u\b", r"\1", expr)
+        expr = re.sub(r"lqs::jit::swz<(\d+)>\((\w+)\)", r"swz(\2, \1)", expr)
+        return expr.replace("lqs::jit::pfold", "pfold").replace("lqs::jit::obit", "obit")
+
     sz = 8 if "lqs::ArF32" in src else 16
     per = 128 // sz
     jt = sj = None
@@ -135,23 +144,24 @@ def _bank_model(src):
         m = re.match(r"(?:uint32_t )?jt = (.*);$", s)
         if m:
             jt = m.group(1)
-        m = re.match(r"const uint32_t (jo\d+) = (.*);$", s)
-        if m:  # adjoint: one swizzled index for the writes of both states
-            named[m.group(1)] = m.group(2)
+        m = re.match(r"const uint32_t ((?:jo|fj)\d+) = (.*);$", s)
+        if m:  # adjoint: one swizzled index for the writes of both states; fj: a folded exchange's write index
+            named[m.group(1)] = (m.group(2), jt)
             continue
         m = re.match(r"\{ const uint32_t sj = (.*);$", s)
         if m:
-            sj = named.get(m.group(1), m.group(1))
+            sj = m.group(1)
             continue
         if sj and ("st_w(&" in s or "ld_w(&" in s):
             c = int(re.search(r"sj \^ (0x[0-9a-f]+)u", s).group(1), 16)
-            expr = re.sub(r"lqs::jit::swz<(\d+)>\(jt\)", r"swz(jt, \1)", sj).replace("lqs::jit::pfold", "pfold")
-            expr = re.sub(r"(0x[0-9a-f]+)u", r"\1", expr)
             for ph in range(32 // per):
                 groups = {}
                 for lane in range(per * ph, per * (ph + 1)):
-                    j = eval(re.sub(r"(0x[0-9a-f]+)u", r"\1", jt).replace("u", ""), {"tid": lane})
-                    a = eval(expr, {"swz": swz, "pfold": pfold, "jt": j}) ^ c
+                    env = {"swz": swz, "pfold": pfold, "obit": obit, "base": 0}
+                    for nm, (ex, jt_then) in named.items():  # each under the jt of its own definition
+                        env[nm] = eval(py(ex), dict(env, jt=eval(py(jt_then), {"tid": lane})))
+                    env["jt"] = eval(py(jt), {"tid": lane})
+                    a = eval(py(sj), env) ^ c
                     groups[a % per] = groups.get(a % per, 0) + 1
                 extra += max(groups.values()) - 1
         elif sj and s.startswith("}"):
@@ -175,11 +185,15 @@ def _unordered_accesses(src):
     def pfold(j, *m):
         return sum((bin(j & mb).count("1") & 1) << b for b, mb in enumerate(m))
 
+    def obit(base, q):
+        return (base >> q) & 1
+
     def ev(expr, **kw):
         expr = re.sub(r"(0x[0-9a-f]+)u", r"\1", expr)
         expr = re.sub(r"(\d+)u\b", r"\1", expr)
         expr = re.sub(r"lqs::jit::swz<(\d+)>\((\w+)\)", r"swz(\2, \1)", expr).replace("lqs::jit::pfold", "pfold")
-        return eval(expr, {"swz": swz, "pfold": pfold}, kw)
+        expr = expr.replace("lqs::jit::obit", "obit")
+        return eval(expr, {"swz": swz, "pfold": pfold, "obit": obit, "base": 0}, kw)
 
     nth = int(re.search(r"__launch_bounds__\((\d+),", src).group(1))
     nw = nth // 32
@@ -195,13 +209,13 @@ def _unordered_accesses(src):
         if m:
             jt = [ev(m.group(1), tid=t) for t in range(nth)]
             continue
-        m = re.match(r"const uint32_t (jo\d+) = (.*);$", s)
+        m = re.match(r"const uint32_t ((?:jo|fj)\d+) = (.*);$", s)
         if m:
-            named[m.group(1)] = [ev(m.group(2), jt=jt[t]) for t in range(nth)]
+            named[m.group(1)] = [ev(m.group(2), jt=jt[t], **{k: v[t] for k, v in named.items()}) for t in range(nth)]
             continue
         m = re.match(r"\{ const uint32_t sj = (.*);$", s)
         if m:
-            sj = named[m.group(1)] if m.group(1) in named else [ev(m.group(1), jt=jt[t]) for t in range(nth)]
+            sj = [ev(m.group(1), jt=jt[t], **{k: v[t] for k, v in named.items()}) for t in range(nth)]
             cur = None
             continue
         m = re.search(r"(st_w|ld_w)\(&(X[AB])\[sj \^ (0x[0-9a-f]+)u\]", s)
@@ -274,4 +288,25 @@ def test_exchanges_are_bank_conflict_free(tmp_path, monkeypatch):
     assert not bad, bad
     # and every pair of conflicting exchange accesses is ordered by barriers
     races = {f: r[:3] for f in files for r in [_unordered_accesses(open(f).read())] if r}
+    assert not races, races
+
+
+def test_permutation_runs_fold_into_exchanges(tmp_path, monkeypatch):
+    """CNOT ladders in compiled segments are folded into the layout exchange
+    that follows them (each amplitude written to its permuted position):
+    generated kernels of the 30-qubit ansatz carry folded exchanges, and the
+    folds stay free of bank conflicts and unordered buffer accesses."""
+    import glob
+    monkeypatch.setenv("LQS_JIT_DUMP", str(tmp_path))
+    c = W.ansatz(30, 3, 3)
+    L.lqs_jit_precompile(30, "c128", c.ops, c.params, L.LQS_ARITH_DF)
+    c = W.ansatz(19, 3, 4)
+    L.lqs_jit_precompile_adjoint(19, "c128", c.ops, c.params, L.LQS_ARITH_DF)
+    files = glob.glob(str(tmp_path / "*.cu"))
+    folded = [f for f in files if "const uint32_t fj" in open(f).read()]
+    assert any("lqs_seg_" in f for f in folded) and any("lqs_adj_" in f for f in folded)
+    assert any("lqs::jit::obit(base" in open(f).read() for f in folded)  # a ladder step controlled from outside
+    bad = {f: e for f in folded for e in [_bank_model(open(f).read())] if e}
+    assert not bad, bad
+    races = {f: r[:3] for f in folded for r in [_unordered_accesses(open(f).read())] if r}
     assert not races, races
