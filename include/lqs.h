@@ -295,10 +295,35 @@ typedef struct {
   double* energy; /* host, 1 entry */
 } lqs_batch_item;
 
-/* Forward + expectation + adjoint gradient of many independent circuits in
- * one captured CUDA graph / persistent launch on `cuda_stream`; fusion width
- * and tile shape come from the autotuner.  Synchronous. */
+/* Forward + expectation + adjoint gradient of many independent circuits
+ * (Listing 1's loop of small circuits) in one persistent launch on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  Every
+ * circuit is a chain of passes over its own state (forward segments, Pauli
+ * passes forming lambda = H psi and the energy, reverse segments with the
+ * gradient partials), one task per tile of the state; resident thread blocks
+ * claim the tasks of all circuits level by level from a shared counter, and a
+ * task waits (bounded: 2 s, LQS_ERR_TIMEOUT) until the tiles of its circuit's
+ * previous pass are done, so the tiles of many circuits run at once on every
+ * SM.  Energies and gradients are summed in a fixed order (deterministic).
+ * Plans are cached by circuit structure; device buffers are kept by the
+ * library between calls (they only grow, and calls are serialised).  The
+ * tile shape of each qubit count is the one lqs_batch_autotune chose, if it
+ * ran, else 2^12 amplitudes (complex64) / 2^11 (complex128) with 32 / 16
+ * contiguous amplitudes per row.  1 <= n_qubits <= 26 per circuit; every
+ * Pauli word's X/Y qubits must fit one tile (LQS_ERR_UNSUPPORTED otherwise).
+ * Synchronous: energies and gradients are in host memory on return. */
 LQS_API int lqs_batch_run(const lqs_batch_item* items, int n_items, int dtype, void* cuda_stream);
+
+/* Autotuner of the batched driver: for each qubit count of the batch that
+ * spans more than one tile, times lqs_batch_run on that count's circuits with
+ * each candidate tile shape (tile qubits k in {12, 11} for complex64, {11, 10}
+ * for complex128; contiguous low qubits b in {5, 4} / {4, 3}), each candidate
+ * run once untimed and `repeats` (1..100) times under CUDA events, and keeps
+ * the fastest per (qubit count, dtype) for later lqs_batch_run calls.  The
+ * items' outputs are written as by lqs_batch_run.  *n_tuned (optional)
+ * receives the number of qubit counts tuned.  Synchronous. */
+LQS_API int lqs_batch_autotune(const lqs_batch_item* items, int n_items, int dtype, void* cuda_stream, int repeats,
+                               int* n_tuned);
 
 /* ---- measurement without device allocation ------------------------------------- */
 

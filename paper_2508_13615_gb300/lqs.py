@@ -107,6 +107,7 @@ def _load():
         "lqs_adjoint_grad": (i32, [vp, ctypes.POINTER(lqs_op), i32, dp, i32, ctypes.POINTER(lqs_pauli), i32, dp,
                                    dp]),
         "lqs_batch_run": (i32, [ctypes.POINTER(lqs_batch_item), i32, i32, vp]),
+        "lqs_batch_autotune": (i32, [ctypes.POINTER(lqs_batch_item), i32, i32, vp, i32, ip]),
         "lqs_last_error": (ctypes.c_char_p, []),
         "lqs_version": (i32, []),
         "lqs_set_arith": (i32, [i32]),
@@ -363,9 +364,7 @@ def lqs_adjoint_grad(h, ops, params, terms) -> Tuple[np.ndarray, float]:
     return g[:npar], e.value
 
 
-def lqs_batch_run(circuits: Sequence, terms_per_circuit: Sequence, dtype, cuda_stream: Optional[int] = None,
-                  grads: bool = True):
-    """Forward + energy (+ adjoint gradients) of many circuits; returns (energies, [grads])."""
+def _batch_items(circuits: Sequence, terms_per_circuit: Sequence, grads: bool):
     m = len(circuits)
     items = (lqs_batch_item * max(m, 1))()
     keep = []
@@ -388,8 +387,26 @@ def lqs_batch_run(circuits: Sequence, terms_per_circuit: Sequence, dtype, cuda_s
         it.terms = pa.ptr()
         it.grads = _dptr(g) if grads else None
         it.energy = ctypes.cast(ctypes.c_void_p(energies.ctypes.data + 8 * i), ctypes.POINTER(ctypes.c_double))
+    return items, keep, energies, gl
+
+
+def lqs_batch_run(circuits: Sequence, terms_per_circuit: Sequence, dtype, cuda_stream: Optional[int] = None,
+                  grads: bool = True):
+    """Forward + energy (+ adjoint gradients) of many circuits; returns (energies, [grads])."""
+    m = len(circuits)
+    items, keep, energies, gl = _batch_items(circuits, terms_per_circuit, grads)
     _check(_L.lqs_batch_run(items, m, _dtype_code(dtype), cuda_stream))
     return energies[:m], gl
+
+
+def lqs_batch_autotune(circuits: Sequence, terms_per_circuit: Sequence, dtype, cuda_stream: Optional[int] = None,
+                       repeats: int = 2, grads: bool = True) -> int:
+    """Times the batch kernel's tile shapes per qubit count and keeps the fastest; returns how many counts were tuned."""
+    m = len(circuits)
+    items, keep, energies, gl = _batch_items(circuits, terms_per_circuit, grads)
+    n = ctypes.c_int()
+    _check(_L.lqs_batch_autotune(items, m, _dtype_code(dtype), cuda_stream, int(repeats), ctypes.byref(n)))
+    return n.value
 
 
 def lqs_last_error() -> str:
