@@ -606,6 +606,14 @@ def config_batch256(args):
         t0 = time.perf_counter()
         e, g = L.lqs_batch_run(circs, terms, "c64")
         tb.append(time.perf_counter() - t0)
+    # device time of the batch's kernels in one call (the rest of the call is host work)
+    L.lqs_profile_start()
+    t0 = time.perf_counter()
+    L.lqs_batch_run(circs, terms, "c64")
+    prof_wall = time.perf_counter() - t0
+    kern = {}
+    for name, ms, _, _ in L.lqs_profile_stop():
+        kern[name] = round(kern.get(name, 0.0) + ms, 3)
     # new parameters, same structures (the next step of a variational loop)
     for c in circs:
         c.params = (c.params + 0.1) % (2 * np.pi)
@@ -631,20 +639,38 @@ def config_batch256(args):
         return es, gs
 
     loop()
+    loop()  # structures used twice: the segment compiler's automatic mode has compiled them now
     torch.cuda.synchronize()
+    jit0 = L.lqs_jit_info()
     tl = []
     for _ in range(2):
         t0 = time.perf_counter()
         el, gl = loop()
         tl.append(time.perf_counter() - t0)
+    jit1 = L.lqs_jit_info()
+    # per qubit count: one pass of the loop over that count's circuits
+    per_n = {}
+    for nq in sorted({c.n_qubits for c in circs}):
+        idx = [i for i, c in enumerate(circs) if c.n_qubits == nq]
+        t0 = time.perf_counter()
+        for i in idx:
+            h = svs[nq].h
+            L.lqs_sv_set_basis(h, 0)
+            L.lqs_apply_fused(h, ops[i], circs[i].params, None)
+            L.lqs_adjoint_grad(h, ops[i], circs[i].params, pas[i])
+        per_n[nq] = round(time.perf_counter() - t0, 4)
     err_e = max(abs(a - b) for a, b in zip(e, el))
     err_g = max(float(np.max(np.abs(a - b))) if len(a) else 0.0 for a, b in zip(g, gl))
     print(json.dumps({"config": "batch256", "circuits": len(circs), "dtype": "c64",
                       "gates": sum(len(c.ops) for c in circs), "params": sum(c.n_params for c in circs),
                       "first_call_s": first_s, "autotune_s": tune_s, "qubit_counts_tuned": tuned,
+                      "one_call_kernel_ms": kern, "one_call_wall_s": prof_wall,
                       "batched_new_params_s": new_params_s,
                       "batched_s": statistics.median(tb), "loop_s": statistics.median(tl),
                       "speedup": statistics.median(tl) / statistics.median(tb),
+                      "loop_s_per_qubit_count": per_n,
+                      "loop_compiled_during_timing": jit1["compiled"] - jit0["compiled"],
+                      "loop_compile_s_during_timing": jit1["compile_seconds"] - jit0["compile_seconds"],
                       "max_abs_energy_batched_minus_loop": err_e, "max_abs_grad_batched_minus_loop": err_g}),
           flush=True)
 

@@ -193,50 +193,114 @@ __global__ void k_distance(const SA* __restrict__ a, const SB* __restrict__ b, u
   }
 }
 
-// Dense-block extraction for the tensor cores.  Ops confined to qubits
-// 0..kBlockQubits-1 gather into a run; ops on other qubits only commute with
-// the run and are deferred past it; an op that touches both ends the run.  A
-// run whose dense weight reaches `threshold` is emitted as one block matrix,
-// otherwise its ops go back into the fused stream (before the deferred ones,
-// which commute with them).  emit(ops, U): U is the block matrix, or null
-// for ops of the fused stream.
+// Dense-block extraction for the tensor cores.  A scan in circuit order keeps
+// open runs, each a set of consecutive gates whose wires stay within one set
+// W of at most kBlockQubits qubits (any qubits; W grows with the run), the
+// runs' sets pairwise disjoint.  A gate joins the one run it touches when W
+// stays within kBlockQubits qubits; otherwise it closes every run it touches
+// and opens a new one.  A closed run whose dense weight reaches the threshold
+// becomes one block.  The other gates keep their circuit order, and each
+// block takes the place of its run's last gate: the gates of the run that it
+// moves past act on other qubits (a gate on W would have joined or closed the
+// run), so they commute with it.  The tensor-core kernel works on qubits
+// 0..kBlockQubits-1: W's qubits above that range are swapped with free
+// qubits of the range before the block (uncontrolled SWAPs, which the fused
+// segments around it apply as relabellings of their tile qubits) and back
+// after it, and the block matrix is composed from the run's gates relabelled
+// the same way.  A window that needs SWAPs must reach twice the threshold,
+// for the passes its SWAPs may add.  emit(ops, U): U is a block matrix, or
+// null for gates of the fused stream.
 template <class Emit>
 static void split_blocks(const std::vector<KOp>& kops, double threshold, Emit&& emit) {
-  const uint64_t win = (1ull << kBlockQubits) - 1;
-  std::vector<int> run, deferred;
-  double weight = 0.0;
-  auto flush = [&]() {
-    if (!run.empty() && weight >= threshold) {
-      double U[2 << (2 * kBlockQubits)];
-      block_matrix(kops, run, U);
-      emit(std::vector<KOp>(), U);
-    } else if (!run.empty()) {
-      std::vector<KOp> v;
-      for (int i : run) v.push_back(kops[i]);
-      emit(std::move(v), nullptr);
-    }
-    if (!deferred.empty()) {
-      std::vector<KOp> v;
-      for (int i : deferred) v.push_back(kops[i]);
-      emit(std::move(v), nullptr);
-    }
-    run.clear();
-    deferred.clear();
-    weight = 0.0;
+  const uint64_t low = (1ull << kBlockQubits) - 1;
+  struct Run {
+    uint64_t W = 0;
+    std::vector<int> ops;
+    double weight = 0.0;
+  };
+  std::vector<Run> open, blocks;
+  auto close = [&](size_t r) {
+    const bool swaps = (open[r].W & ~low) != 0;
+    if (open[r].weight >= (swaps ? 2.0 : 1.0) * threshold) blocks.push_back(open[r]);
+    open.erase(open.begin() + (long)r);
   };
   for (int i = 0; i < (int)kops.size(); ++i) {
     const uint64_t w = kops[i].wire_mask();
-    if (!(w & ~win)) {
-      run.push_back(i);
-      weight += block_weight(kops[i]);
-    } else if (!(w & win)) {
-      deferred.push_back(i);
-    } else {
-      flush();
-      emit(std::vector<KOp>{kops[i]}, nullptr);
+    std::vector<size_t> hit;
+    for (size_t r = 0; r < open.size(); ++r)
+      if (open[r].W & w) hit.push_back(r);
+    if (hit.size() == 1 && __builtin_popcountll(open[hit[0]].W | w) <= kBlockQubits) {
+      Run& R = open[hit[0]];
+      R.W |= w;
+      R.ops.push_back(i);
+      R.weight += block_weight(kops[i]);
+      continue;
+    }
+    for (size_t h = hit.size(); h-- > 0;) close(hit[h]);
+    if (__builtin_popcountll(w) <= kBlockQubits) {
+      Run R;
+      R.W = w;
+      R.ops.push_back(i);
+      R.weight = block_weight(kops[i]);
+      open.push_back(std::move(R));
     }
   }
-  flush();
+  while (!open.empty()) close(open.size() - 1);
+  // the output: gates in circuit order, each block in place of its run's last gate
+  std::vector<int> block_of(kops.size(), -1), last_of(kops.size(), -1);
+  for (size_t bI = 0; bI < blocks.size(); ++bI) {
+    for (int i : blocks[bI].ops) block_of[(size_t)i] = (int)bI;
+    last_of[(size_t)blocks[bI].ops.back()] = (int)bI;
+  }
+  std::vector<KOp> pending;
+  auto flush_pending = [&]() {
+    if (!pending.empty()) emit(std::move(pending), nullptr);
+    pending.clear();
+  };
+  for (int i = 0; i < (int)kops.size(); ++i) {
+    if (block_of[(size_t)i] < 0) {
+      pending.push_back(kops[i]);
+      continue;
+    }
+    if (last_of[(size_t)i] < 0) continue;
+    const Run& R = blocks[(size_t)last_of[(size_t)i]];
+    // map: each qubit of W above the range takes a free qubit of the range
+    int to[64];
+    for (int q = 0; q < 64; ++q) to[q] = q;
+    std::vector<KOp> sw;
+    uint64_t freel = low & ~R.W;
+    for (uint64_t hi = R.W & ~low; hi; hi &= hi - 1) {
+      const int q = __builtin_ctzll(hi);
+      const int sl = __builtin_ctzll(freel);
+      freel &= freel - 1;
+      to[q] = sl;
+      to[sl] = q;
+      KOp k;
+      k.kind = K_SWAP;
+      k.t0 = sl;
+      k.t1 = q;
+      sw.push_back(k);
+    }
+    std::vector<KOp> rel;
+    for (int j : R.ops) {
+      KOp k = kops[(size_t)j];
+      if (k.t0 >= 0) k.t0 = to[k.t0];
+      if (k.t1 >= 0) k.t1 = to[k.t1];
+      uint64_t cm = 0;
+      for (uint64_t c = k.cmask; c; c &= c - 1) cm |= 1ull << to[__builtin_ctzll(c)];
+      k.cmask = cm;
+      rel.push_back(k);
+    }
+    std::vector<int> all(rel.size());
+    for (size_t j = 0; j < all.size(); ++j) all[j] = (int)j;
+    double U[2 << (2 * kBlockQubits)];
+    block_matrix(rel, all, U);
+    pending.insert(pending.end(), sw.begin(), sw.end());
+    flush_pending();
+    emit(std::vector<KOp>(), U);
+    pending.insert(pending.end(), sw.begin(), sw.end());
+  }
+  flush_pending();
 }
 
 }  // namespace lqs

@@ -158,3 +158,39 @@ def test_fused_path_extracts_tensor_core_blocks(n):
         assert (blocks > 0) == (mode == "on"), (mode, blocks)
         assert max_abs(got[mode], want) <= TOL["c64"], mode
     assert max_abs(got["on"], got["off"]) <= TOL["c64"]
+
+
+def _window_run(c, window, count, seed):
+    """`count` Haar U4 gates on neighbouring pairs of `window` (five qubits)."""
+    for g in range(count):
+        i = (3 * g) % 4
+        c.add("U4", (window[i + 1], window[i]), matrix=W.haar_unitary(4, seed, g))
+
+
+@pytest.mark.parametrize("n", [14, 17, 20])
+def test_blocks_on_other_windows(n):
+    """Heavy runs on five qubits anywhere in the state (consecutive, spread
+    out, the top five) become tensor-core blocks: the fused planner swaps the
+    window onto qubits 0..4 around each block (SWAPs it applies as tile
+    relabellings) and composes the block from the relabelled gates."""
+    L = _lib()
+    windows = [(5, 6, 7, 8, 9), (2, 6, 9, 11, n - 2), tuple(range(n - 5, n))]
+    c = W.Circuit(n)
+    c.add("H", (0,))
+    for k, win in enumerate(windows):
+        _window_run(c, win, 12, 700 + k)
+        c.add("CNOT", (win[0], 0))  # a gate taking a sixth qubit ends the run
+    psi0 = W.gaussian_state(n, 710 + n)
+    want = oracle.run_circuit(c, psi0)
+    got = {}
+    for mode, cfg in (("on", None), ("off", {"tc_blocks": -1})):
+        with gpu_state(n, "c64", psi0) as sv:
+            L.lqs_profile_start()
+            sv.apply(c, fused=True, cfg=cfg)
+            recs = L.lqs_profile_stop()
+            got[mode] = sv.numpy()
+        blocks = sum(1 for r in recs if r[0].startswith("k_block_tc"))
+        assert blocks == (len(windows) if mode == "on" else 0), (mode, blocks)
+        err = max_abs(got[mode], want)
+        assert err <= TOL["c64"], (mode, err)
+        assert err <= REL * np.max(np.abs(want)) * 4, (mode, err)
