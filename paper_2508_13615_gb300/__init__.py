@@ -13,14 +13,15 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import lqs
-from .lqs import (GATE_IDS, LQS_ARITH_AUTO, LQS_ARITH_DF, LQS_ARITH_F64, LQS_C64, LQS_C128, LQS_JIT_AUTO, LQS_JIT_OFF,
+from .lqs import (BatchItems, GATE_IDS, LQS_ARITH_AUTO, LQS_ARITH_DF, LQS_ARITH_F64, LQS_C64, LQS_C128, LQS_JIT_AUTO, LQS_JIT_OFF,
                   LQS_JIT_ON, LqsError, OpArray,
                   PauliArray, lqs_adjoint_grad, lqs_apply_fused, lqs_apply_gate, lqs_apply_matrix, lqs_autotune_fused, lqs_batch_autotune, lqs_batch_run,
                   lqs_debug_df_roundtrip, lqs_expval, lqs_expval_static, lqs_jit_info, lqs_jit_precompile, lqs_jit_precompile_adjoint, lqs_jit_precompile_expval, lqs_kernel_launches, lqs_last_error, lqs_norm2,
                   lqs_plan_fused, lqs_profile_start, lqs_profile_stop, lqs_set_arith, lqs_set_jit, lqs_sv_alloc, lqs_sv_copy_from_host, lqs_sv_copy_to_host, lqs_sv_copy_to_host_async, lqs_apply_block, lqs_block_matrix, lqs_sv_distance,
                   lqs_sv_free, lqs_sv_info, lqs_sv_set_basis, lqs_sv_sync, lqs_version, lqs_check_bounded_wait)
 
-__all__ = [n for n in dir(lqs) if n.startswith("lqs_")] + ["StateVector", "ExpvalFunction", "expval_autograd"]
+__all__ = [n for n in dir(lqs) if n.startswith("lqs_")] + ["BatchItems", "StateVector", "ExpvalFunction",
+                                                             "expval_autograd"]
 
 
 class StateVector:

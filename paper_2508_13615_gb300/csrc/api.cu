@@ -194,11 +194,11 @@ __global__ void k_distance(const SA* __restrict__ a, const SB* __restrict__ b, u
 }
 
 // Dense-block extraction for the tensor cores.  A scan in circuit order keeps
-// open runs, each a set of consecutive gates whose wires stay within one set
-// W of at most kBlockQubits qubits (any qubits; W grows with the run), the
-// runs' sets pairwise disjoint.  A gate joins the one run it touches when W
-// stays within kBlockQubits qubits; otherwise it closes every run it touches
-// and opens a new one.  A closed run whose dense weight reaches the threshold
+// open runs, each a set of gates whose wires stay within one set W of at
+// most kBlockQubits qubits (any qubits; W grows with the run), the runs' sets
+// pairwise disjoint.  A gate joins the runs it touches, merged into one, when
+// their qubits and its own number at most kBlockQubits; otherwise it closes
+// every run it touches and opens a new one.  A closed run whose dense weight reaches the threshold
 // becomes one block.  The other gates keep their circuit order, and each
 // block takes the place of its run's last gate: the gates of the run that it
 // moves past act on other qubits (a gate on W would have joined or closed the
@@ -229,9 +229,19 @@ static void split_blocks(const std::vector<KOp>& kops, double threshold, Emit&& 
     std::vector<size_t> hit;
     for (size_t r = 0; r < open.size(); ++r)
       if (open[r].W & w) hit.push_back(r);
-    if (hit.size() == 1 && __builtin_popcountll(open[hit[0]].W | w) <= kBlockQubits) {
+    uint64_t uni = w;
+    for (size_t r : hit) uni |= open[r].W;
+    if (!hit.empty() && __builtin_popcountll(uni) <= kBlockQubits) {
+      // the gate joins the runs it touches, merged into one (their gates in circuit order)
       Run& R = open[hit[0]];
-      R.W |= w;
+      for (size_t h = hit.size(); h-- > 1;) {
+        Run& Q = open[hit[h]];
+        R.ops.insert(R.ops.end(), Q.ops.begin(), Q.ops.end());
+        R.weight += Q.weight;
+        open.erase(open.begin() + (long)hit[h]);
+      }
+      std::sort(R.ops.begin(), R.ops.end());
+      R.W = uni;
       R.ops.push_back(i);
       R.weight += block_weight(kops[i]);
       continue;

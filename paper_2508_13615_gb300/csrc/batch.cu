@@ -85,6 +85,7 @@ template <class A>
 struct QArgs {
   const QStage* stages;
   int nstages;
+  const int* task_stage;   // per task: its stage
   const int* circ_stages;  // per circuit: the stage indices of its Pauli passes, then of its reverse segments
   const QCirc* circ;
   int ncirc;
@@ -165,13 +166,7 @@ __global__ void __launch_bounds__(kTileThreads) k_batch(const QArgs<A> a) {
       const uint32_t t = atomicAdd(a.counter, 1);
       int st = -1;
       if (t < a.ntasks && !ld_acquire(a.abort)) {
-        int lo = 0, hi = a.nstages - 1;  // the last stage whose first task is <= t
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.stages[mid].task0 <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        st = lo;
+        st = a.task_stage[t];
         const int dep = a.stages[st].dep;
         if (dep >= 0 && !wait_count(a.done + dep, (int)a.stages[dep].g.ntiles, a.abort)) {
           if (atomicCAS(a.status, 0, 4) == 0) a.status[1] = (int)blockIdx.x;
@@ -696,7 +691,12 @@ static int batch_run_t(const lqs_batch_item* items, int n_items, int dtype, cuda
     off += bytes;
     return at;
   };
+  std::vector<int> task_stage(ntasks);
+  for (size_t si = 0; si < stages.size(); ++si)
+    std::fill(task_stage.begin() + stages[si].task0, task_stage.begin() + stages[si].task0 + stages[si].g.ntiles,
+              (int)si);
   const size_t o_st = place(sizeof(QStage) * stages.size());
+  const size_t o_ts = place(sizeof(int) * std::max<size_t>(ntasks, 1));
   const size_t o_cs = place(sizeof(int) * std::max<size_t>(circ_stages.size(), 1));
   const size_t o_ci = place(sizeof(QCirc) * circ.size());
   const size_t o_op = place(sizeof(TOp) * std::max<size_t>(ops.size(), 1));
@@ -717,6 +717,7 @@ static int batch_run_t(const lqs_batch_item* items, int n_items, int dtype, cuda
     if (bytes) std::memcpy(h + at, src, bytes);
   };
   put(o_st, stages.data(), sizeof(QStage) * stages.size());
+  put(o_ts, task_stage.data(), sizeof(int) * task_stage.size());
   put(o_cs, circ_stages.data(), sizeof(int) * circ_stages.size());
   put(o_ci, circ.data(), sizeof(QCirc) * circ.size());
   put(o_op, ops.data(), sizeof(TOp) * ops.size());
@@ -732,6 +733,7 @@ static int batch_run_t(const lqs_batch_item* items, int n_items, int dtype, cuda
   QArgs<A> a{};
   a.stages = reinterpret_cast<const QStage*>(d + o_st);
   a.nstages = (int)stages.size();
+  a.task_stage = reinterpret_cast<const int*>(d + o_ts);
   a.circ_stages = reinterpret_cast<const int*>(d + o_cs);
   a.circ = reinterpret_cast<const QCirc*>(d + o_ci);
   a.ncirc = n_items;

@@ -390,6 +390,28 @@ def _batch_items(circuits: Sequence, terms_per_circuit: Sequence, grads: bool):
     return items, keep, energies, gl
 
 
+class BatchItems:
+    """The lqs_batch_item array of a batch, marshalled once.  `params[i]` is
+    circuit i's parameter array as the library reads it: a variational loop
+    writes new values into it in place and calls run() again."""
+
+    def __init__(self, circuits: Sequence, terms_per_circuit: Sequence, grads: bool = True):
+        self.m = len(circuits)
+        self.items, self._keep, self._energies, self._grads = _batch_items(circuits, terms_per_circuit, grads)
+        self.params = [self._keep[4 * i + 2] for i in range(self.m)]
+
+    def run(self, dtype, cuda_stream: Optional[int] = None):
+        """lqs_batch_run on the marshalled items; returns (energies, [grads]) (views, overwritten by the next run)."""
+        _check(_L.lqs_batch_run(self.items, self.m, _dtype_code(dtype), cuda_stream))
+        return self._energies[: self.m], self._grads
+
+    def autotune(self, dtype, cuda_stream: Optional[int] = None, repeats: int = 2) -> int:
+        n = ctypes.c_int()
+        _check(_L.lqs_batch_autotune(self.items, self.m, _dtype_code(dtype), cuda_stream, int(repeats),
+                                     ctypes.byref(n)))
+        return n.value
+
+
 def lqs_batch_run(circuits: Sequence, terms_per_circuit: Sequence, dtype, cuda_stream: Optional[int] = None,
                   grads: bool = True):
     """Forward + energy (+ adjoint gradients) of many circuits; returns (energies, [grads])."""
