@@ -319,7 +319,7 @@ def sources_digest(paths) -> str:
 SEG_SOURCES = ("paper_2508_13615_gb300/csrc/jit.cu", "paper_2508_13615_gb300/csrc/jit_dev.cuh",
                "paper_2508_13615_gb300/csrc/tile.cuh", "paper_2508_13615_gb300/csrc/arith.cuh",
                "paper_2508_13615_gb300/csrc/fused_reg.cu")
-BLOCK_SOURCES = ("paper_2508_13615_gb300/csrc/block_tc.cu",)
+BLOCK_SOURCES = ("paper_2508_13615_gb300/csrc/block_tc.cu", "paper_2508_13615_gb300/csrc/tile.cuh")
 DENSE_SOURCES = ("paper_2508_13615_gb300/csrc/gate_kernels.cu", "paper_2508_13615_gb300/csrc/arith.cuh",
                  "paper_2508_13615_gb300/csrc/gates.cu")
 

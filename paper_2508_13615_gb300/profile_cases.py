@@ -10,8 +10,10 @@ expectation, three times), ``adjoint`` (adjoint gradient of a 2-layer
 ansatz), ``gate`` (one dense H per qubit on the plain path), ``u4`` (the
 Haar 4x4 gates of the single-gate sweep, U4(t, t+1), on the plain path),
 ``block`` (a Haar 32x32 block on qubits 0..4 on the tensor cores, three
-times; complex64 only), ``rz`` (one RZ per qubit) and ``cnot`` (CNOT from the
-highest qubit to every other one), both on the plain path.  States start at
+times; complex64 only), ``batch`` (64 ansatz circuits of 10..N qubits with
+their TFIM energies and gradients through the batched driver, twice), ``rz``
+(one RZ per qubit) and ``cnot`` (CNOT from the highest qubit to every other
+one), both on the plain path.  States start at
 |0..0>; the sizes default to 24 qubits so the state (256 MiB complex128)
 exceeds the 129 MB L2 while a full ncu capture stays short.
 """
@@ -69,6 +71,13 @@ def main(argv=None) -> None:
         sv.apply_gate("H", (n - 1,))
         for q in range(n - 1):
             sv.apply_gate("CNOT", (n - 1, q))
+    elif mode == "batch":
+        # a batch of 64 ansatz circuits of 10..n qubits through the task-queue kernel
+        circs = W.batch_circuits(64, 7, n_min=10, n_max=n)
+        terms = [W.tfim(c.n_qubits) for c in circs]
+        B = L.BatchItems(circs, terms)
+        for _ in range(2):
+            B.run(dtype)
     elif mode == "u4":
         for _, c in W.sweep_30q(n):
             if c.ops[0].name == "U4":

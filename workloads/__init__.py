@@ -394,13 +394,14 @@ def sweep_30q(n: int = 30, seed: int = 2) -> List[Tuple[str, Circuit]]:
     return out
 
 
-def batch_circuits(count: int = 256, seed: int = 7) -> List[Circuit]:
-    """Ragged batch: circuit i has n ~ U{10..20} qubits and L ~ U{4..12} layers
-    of the ansatz, with parameters from stream ``seed + i``."""
+def batch_circuits(count: int = 256, seed: int = 7, n_min: int = 10, n_max: int = 20) -> List[Circuit]:
+    """Ragged batch: circuit i has n ~ U{n_min..n_max} qubits (10..20 by
+    default) and L ~ U{4..12} layers of the ansatz, with parameters from
+    stream ``seed + i``."""
     r = splitmix64(seed, 0, 2 * count)
     out = []
     for i in range(count):
-        n = 10 + int(r[2 * i] % np.uint64(11))
+        n = n_min + int(r[2 * i] % np.uint64(n_max - n_min + 1))
         L = 4 + int(r[2 * i + 1] % np.uint64(9))
         out.append(ansatz(n, L, seed + i))
     return out
