@@ -329,11 +329,11 @@ DENSE_SOURCES = ("paper_2508_13615_gb300/csrc/gate_kernels.cu", "paper_2508_1361
 # entry names the profile summary it comes from and the digest of the sources
 # at capture time; `traffic` is null whenever the sources have changed since.
 TRAFFIC = {
-    "k_fused_reg_jit/df": {"read": 268.6e6, "write": 213.3e6, "capture_qubits": 24,
+    "k_fused_reg_jit/df": {"read": 268.581376e6, "write": 206.119680e6, "capture_qubits": 24,
                            "source": "profiles/compiled_segment_ansatz_24q_c128.md",
-                           "files": SEG_SOURCES, "sha": None},
-    "k_block_tc": {"read": 537.0e6, "write": 475.1e6, "capture_qubits": 26,
-                   "source": "profiles/k_block_tc_tf32x3_26q_c64.md", "files": BLOCK_SOURCES, "sha": None},
+                           "files": SEG_SOURCES, "sha": "0a02e8f4ede45bb0"},
+    "k_block_tc": {"read": 537.046528e6, "write": 475.009792e6, "capture_qubits": 26,
+                   "source": "profiles/k_block_tc_tf32x3_26q_c64.md", "files": BLOCK_SOURCES, "sha": "38c07247c2d88ac4"},
 }
 
 
@@ -516,9 +516,20 @@ def adjoint_leg(steps: int, warmup: int, n: int = 24, layers: int = 8):
                 e1.record(st)
                 torch.cuda.synchronize()
                 ta.append(e0.elapsed_time(e1))
+            # device time per kernel family of one forward and one adjoint call
+            parts = {}
+            for key, fn in (("forward", fwd), ("adjoint", lambda: L.lqs_adjoint_grad(sv.h, ops, c.params, pa))):
+                if key == "adjoint":
+                    fwd()
+                L.lqs_profile_start()
+                fn()
+                fam = {}
+                for name, ms, _, _ in L.lqs_profile_stop():
+                    fam[name] = round(fam.get(name, 0.0) + ms, 3)
+                parts[key] = fam
             rec = {"forward_ms": statistics.median(tf), "adjoint_ms": statistics.median(ta),
                    "adjoint_over_forward": statistics.median(ta) / statistics.median(tf), "energy": e,
-                   "compile_wall_s": round(jit_s, 2)}
+                   "kernel_ms": parts, "compile_wall_s": round(jit_s, 2)}
             if dtype == "c128":
                 h = 1e-6
                 fd = []

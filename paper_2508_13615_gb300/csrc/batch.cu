@@ -289,8 +289,7 @@ __global__ void __launch_bounds__(kTileThreads) k_batch(const QArgs<A> a) {
           const DF v = warp_sum(gen_partial<A>(Pt, Lt, o, base, G.k));
           if (lane == 0) wacc[warp * kMaxGradSlots + o.gslot] = df2d(v);
         }
-        tile_apply<A>(Pt, o, coef, base, G.k);
-        tile_apply<A>(Lt, o, coef, base, G.k);
+        tile_apply2<A>(Pt, Lt, o, coef, base, G.k);
         __syncthreads();
       }
       for (uint32_t j = tid; j < nt; j += nth) {

@@ -526,8 +526,7 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint(typename A::S* __restr
         const DF s = warp_sum(gen_partial<A>(Pt, Lt, o, base, G.k));
         if (lane == 0) wacc[warp * kMaxGradSlots + o.gslot] += df2d(s);
       }
-      tile_apply<A>(Pt, o, P.coef, base, G.k);
-      tile_apply<A>(Lt, o, P.coef, base, G.k);
+      tile_apply2<A>(Pt, Lt, o, P.coef, base, G.k);
       __syncthreads();
     }
     if constexpr (!std::is_same<S, W>::value) {

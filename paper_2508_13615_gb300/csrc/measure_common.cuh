@@ -10,6 +10,7 @@
 #include "arith.cuh"
 #include "lqs_internal.cuh"
 #include "tile.cuh"
+#include "tile_ops.cuh"
 
 namespace lqs {
 
@@ -145,9 +146,9 @@ inline int lpos(const TileGeom& G, int q) {
 constexpr int kMaxGradSlots = 128;
 
 // Im <lambda|G|psi> over the tile for generator G of op o (before U^dagger).
-template <class A>
-__device__ __forceinline__ DAcc gen_partial(const typename A::W* Ps, const typename A::W* Ls, const TOp& o,
-                                            uint64_t base, int k) {
+template <class A, int NF>
+__device__ __forceinline__ DAcc gen_partial_n(const typename A::W* Ps, const typename A::W* Ls, const TOp& o,
+                                              uint64_t base, int k, const uint32_t (&mk)[5]) {
   DAcc acc{0.f, 0.f};
   const uint32_t tid = threadIdx.x, nth = blockDim.x;
   const uint32_t lc = o.lcmask;
@@ -157,7 +158,7 @@ __device__ __forceinline__ DAcc gen_partial(const typename A::W* Ps, const typen
     const bool neg = (o.gen == G_Z) && (base & o.e0);
     const uint32_t ng = 1u << (k - o.nfix);
     for (uint32_t g = tid; g < ng; g += nth) {
-      const uint32_t j = ins0(g, o.fix, o.nfix) | lc;
+      const uint32_t j = ins_m<NF>(g, mk) | lc;
       acc_im_conj(acc, to_dfc(Ls[j]), to_dfc(Ps[j]), neg);
     }
     return acc;
@@ -165,7 +166,7 @@ __device__ __forceinline__ DAcc gen_partial(const typename A::W* Ps, const typen
   const uint32_t tb = 1u << o.l0;
   const uint32_t ng = 1u << (k - o.nfix);
   for (uint32_t g = tid; g < ng; g += nth) {
-    const uint32_t j0 = ins0(g, o.fix, o.nfix) | lc, j1 = j0 | tb;
+    const uint32_t j0 = ins_m<NF>(g, mk) | lc, j1 = j0 | tb;
     const DFC p0 = to_dfc(Ps[j0]), p1 = to_dfc(Ps[j1]), l0 = to_dfc(Ls[j0]), l1 = to_dfc(Ls[j1]);
     if (o.gen == G_X) {  // conj(l0) p1 + conj(l1) p0
       acc_im_conj(acc, l0, p1, false);
@@ -179,6 +180,20 @@ __device__ __forceinline__ DAcc gen_partial(const typename A::W* Ps, const typen
     }
   }
   return acc;
+}
+
+template <class A>
+__device__ __forceinline__ DAcc gen_partial(const typename A::W* Ps, const typename A::W* Ls, const TOp& o,
+                                            uint64_t base, int k) {
+  uint32_t mk[5];
+  ins_masks(o, mk);
+  switch (o.nfix) {
+    case 0: return gen_partial_n<A, 0>(Ps, Ls, o, base, k, mk);
+    case 1: return gen_partial_n<A, 1>(Ps, Ls, o, base, k, mk);
+    case 2: return gen_partial_n<A, 2>(Ps, Ls, o, base, k, mk);
+    case 3: return gen_partial_n<A, 3>(Ps, Ls, o, base, k, mk);
+    default: return gen_partial_n<A, 4>(Ps, Ls, o, base, k, mk);
+  }
 }
 
 // U^dagger of a lowered op (same kernel class, conjugate-transposed entries).
