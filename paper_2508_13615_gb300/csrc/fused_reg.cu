@@ -53,6 +53,15 @@ template <> struct RegR<ArF32> { static constexpr int R = 16; };
 
 int reg_tile_qubits(int dtype) { return (dtype == LQS_C64 ? 4 : 3) + kRegThreadBits; }
 
+// Register bits per thread of a compiled forward segment.  The tile keeps its
+// reg_tile_qubits; fewer register bits give more threads per tile (2^(k - r)).
+// The interpreter keeps RegR's count.
+#ifndef LQS_SEG_RBITS_C128
+#define LQS_SEG_RBITS_C128 3
+#endif
+template <class A> struct JitR { static constexpr int r = LQS_SEG_RBITS_C128; };
+template <> struct JitR<ArF32> { static constexpr int r = 4; };
+
 // ---------------------------------------------------------------------------
 // device side
 // ---------------------------------------------------------------------------
@@ -786,20 +795,21 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
 template <class A>
 int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {
   constexpr int R = RegR<A>::R;
-  const int r = RLog<R>::r;
+  const int r = RLog<R>::r, rj = JitR<A>::r;
   static thread_local TileProg<A> P;
   init_prog(P, sv->n, seg.qmask, k, b);
-  const bool fold = jit_enabled_for(sv->n);  // compiled segments fold permutation runs into exchanges
-  LQS_TRY(build_reg_prog(P, ops, seg, r, nullptr, fold));
+  const bool jit = jit_enabled_for(sv->n);  // compiled segments fold permutation runs into exchanges
+  LQS_TRY(build_reg_prog(P, ops, seg, jit ? rj : r, nullptr, jit));
   double flops = 0.0;
   for (int i : seg.ops) flops += kop_touched_fraction(ops[i]) * kop_flops_per_amp(ops[i]);
   {
     bool launched = false;
     const std::string jname = std::string("k_fused_reg_jit/") + arith_tag(sv->dtype, arith);
-    LQS_TRY(jit_launch(P, r, sv, 2.0 * (double)sv->bytes(), flops * (double)sv->N(), jname.c_str(), &launched));
+    LQS_TRY(jit_launch(P, jit ? rj : r, sv, 2.0 * (double)sv->bytes(), flops * (double)sv->N(), jname.c_str(),
+                       &launched));
     if (launched) return LQS_OK;
   }
-  if (P.nfold) {  // the interpreter applies every gate itself: the same segment without folds
+  if (P.nfold || (jit && rj != r)) {  // the interpreter: every gate applied by itself, its own register count
     init_prog(P, sv->n, seg.qmask, k, b);
     LQS_TRY(build_reg_prog(P, ops, seg, r));
   }
@@ -828,8 +838,8 @@ static int note_reg_prog_t(int n, const std::vector<KOp>& ops, const Segment& se
   constexpr int R = RegR<A>::R;
   static thread_local TileProg<A> P;
   init_prog(P, n, seg.qmask, k, b);
-  LQS_TRY(build_reg_prog(P, ops, seg, RLog<R>::r, nullptr, true));
-  return jit_note(P, RLog<R>::r, n, force, todo);
+  LQS_TRY(build_reg_prog(P, ops, seg, JitR<A>::r, nullptr, true));
+  return jit_note(P, JitR<A>::r, n, force, todo);
 }
 
 int note_reg_prog(int n, int dtype, int arith, const std::vector<KOp>& ops, const Segment& seg, int k, int b,
