@@ -572,11 +572,16 @@ def config_precision32(args):
     c = W.ansatz(n, 20, 5)
     terms = W.zz_chain(n)
     ops = L.OpArray(c.ops)
-    res = {"config": "precision32", "n_qubits": n, "layers": 20, "gates": len(c.ops)}
+    res = {"config": "precision32", "n_qubits": n, "layers": 20, "gates": len(c.ops),
+           "timing": "second application (the segment kernels are compiled before the first), CUDA events"}
     svs = {}
+    L.lqs_set_jit(L.LQS_JIT_ON)
     for dtype in ("c128", "c64"):
+        L.lqs_jit_precompile(n, dtype, c.ops, c.params, L.LQS_ARITH_DF if dtype == "c128" else L.LQS_ARITH_AUTO)
         sv = L.StateVector(n, dtype)
         st = torch.cuda.current_stream()
+        L.lqs_sv_set_basis(sv.h, 0)
+        L.lqs_apply_fused(sv.h, ops, c.params, None)
         e0, e1 = _events()
         e0.record(st)
         L.lqs_sv_set_basis(sv.h, 0)
