@@ -221,7 +221,13 @@ LQS_API int lqs_block_matrix(const lqs_op* ops, int n_ops, const double* params,
  * plus chosen high qubits); each segment is one HBM pass in which the tile is
  * staged in shared memory by bulk asynchronous copies and all of its gates are
  * applied on chip.  Gates on disjoint wires may be reordered; the result equals
- * applying ops[0..n_ops) in order.  params: the circuit's parameter array. */
+ * applying ops[0..n_ops) in order.  params: the circuit's parameter array.
+ * Between consecutive compiled complex128 segments of one call the state is
+ * held as pairs of float32 (the double-float working format); the call's
+ * last segment writes complex128 again, so the state is complex128 whenever
+ * work queued after the call (or on another stream after synchronising) reads
+ * it.  If the call returns an error after launching, the state is
+ * unspecified. */
 LQS_API int lqs_apply_fused(lqs_sv* sv, const lqs_op* ops, int n_ops, const double* params, int n_params,
                     const lqs_fuse_cfg* cfg_or_null);
 

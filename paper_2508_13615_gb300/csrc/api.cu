@@ -588,9 +588,28 @@ int lqs_apply_fused(lqs_sv* h, const lqs_op* ops, int n_ops, const double* param
     const int rc = jit_compile(todo);
     if (rc != LQS_OK && jit_mode() == LQS_JIT_ON) return rc;
   }
+  // Consecutive compiled double-float segments hand the state to one another
+  // as hi/lo float pairs (no float64 conversions in between); the first
+  // reads float64 and the last writes it, so the call leaves a complex128
+  // state as always.
+  std::vector<std::pair<const Piece*, const Segment*>> order;
   for (auto& p : pieces) {
-    if (p->block) LQS_TRY(apply_block(sv, p->U));
-    for (const Segment& s : p->segs) LQS_TRY(launch_segment(sv, p->ops, s, pc, arith));
+    if (p->block) order.emplace_back(p.get(), nullptr);
+    for (const Segment& s : p->segs) order.emplace_back(p.get(), &s);
+  }
+  const int kk = std::min(pc.k, sv->n), bb = std::min(pc.b, kk);
+  std::vector<char> split(order.size(), 0);
+  for (size_t i = 0; i < order.size(); ++i)
+    split[i] = order[i].second && seg_split_capable(sv, order[i].first->ops, *order[i].second, kk, bb, arith);
+  for (size_t i = 0; i < order.size(); ++i) {
+    const Piece* p = order[i].first;
+    if (!order[i].second) {
+      LQS_TRY(apply_block(sv, p->U));
+      continue;
+    }
+    const unsigned fmt = split[i] ? (i > 0 && split[i - 1] ? 1u : 0u) | (i + 1 < order.size() && split[i + 1] ? 2u : 0u)
+                                  : 0u;
+    LQS_TRY(launch_segment(sv, p->ops, *order[i].second, pc, arith, fmt));
   }
   return LQS_OK;
 }

@@ -212,9 +212,11 @@ int add_tile_op(TileProg<A>& P, const KOp& o, int gslot) {
   // an uncontrolled real 2x2 with m11 = s m00 and m10 = -s m01 (s = +1:
   // rotations such as RY, special 1; s = -1: reflections such as H, special 2)
   // is g times an orthogonal matrix: compiled segments apply it in a cheaper
-  // form (the interpreter ignores the mark)
+  // form (the interpreter ignores the mark).  Special 3: the Hadamard pattern
+  // m00 = m01 = m10 = -m11 > 0, sums and differences only.
   if (o.kind == K_DENSE1R && o.cmask == 0) {
     if (o.m[3] == o.m[0] && o.m[2] == -o.m[1]) t.special = 1;
+    else if (o.m[0] > 0.0 && o.m[1] == o.m[0] && o.m[2] == o.m[0] && o.m[3] == -o.m[0]) t.special = 3;
     else if (o.m[3] == -o.m[0] && o.m[2] == o.m[1]) t.special = 2;
   }
   P.op[P.nops++] = t;
@@ -313,10 +315,12 @@ static int launch_fused_t(SV* sv, const std::vector<KOp>& ops, const Segment& se
   return LQS_OK;
 }
 
-int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith) {
+int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith,
+                   unsigned fmt) {
+  const int k = std::min(pc.k, sv->n), b = std::min(pc.b, k);
+  if (fmt) return launch_fused_reg(sv, ops, seg, k, b, arith, fmt);  // checked by seg_split_capable
   // A lone gate is cheaper as a plain pass: it only touches the amplitudes it changes.
   if (seg.ops.size() == 1) return launch_gate(sv, ops[seg.ops[0]], arith);
-  const int k = std::min(pc.k, sv->n), b = std::min(pc.b, k);
   if (k == reg_tile_qubits(sv->dtype)) {
     const int rc = launch_fused_reg(sv, ops, seg, k, b, arith);
     if (rc != LQS_ERR_UNSUPPORTED) return rc;

@@ -793,7 +793,8 @@ static int build_reg_prog(TileProg<A>& P, const std::vector<KOp>& ops, const Seg
 }
 
 template <class A>
-int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {
+int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith,
+                       unsigned fmt) {
   constexpr int R = RegR<A>::R;
   const int r = RLog<R>::r, rj = JitR<A>::r;
   static thread_local TileProg<A> P;
@@ -806,9 +807,10 @@ int launch_fused_reg_t(SV* sv, const std::vector<KOp>& ops, const Segment& seg, 
     bool launched = false;
     const std::string jname = std::string("k_fused_reg_jit/") + arith_tag(sv->dtype, arith);
     LQS_TRY(jit_launch(P, jit ? rj : r, sv, 2.0 * (double)sv->bytes(), flops * (double)sv->N(), jname.c_str(),
-                       &launched));
+                       &launched, fmt));
     if (launched) return LQS_OK;
   }
+  if (fmt) return set_error(LQS_ERR_CUDA, "internal: a segment planned as compiled code was not launched");
   if (P.nfold || (jit && rj != r)) {  // the interpreter: every gate applied by itself, its own register count
     init_prog(P, sv->n, seg.qmask, k, b);
     LQS_TRY(build_reg_prog(P, ops, seg, r));
@@ -967,12 +969,16 @@ static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam
   double* partial = static_cast<double*>(scratch);
   const std::string pname = std::string("k_adjoint_jit/") + arith_tag(sv->dtype, arith);
   size_t off = 0;
-  for (auto& pr : progs) {
+  for (size_t j = 0; j < progs.size(); ++j) {
+    auto& pr = progs[j];
     // both states un-apply every op; each gradient slot is about 8 flops per amplitude
     double fl = 8.0 * (double)pr->gops.size();
     for (int i : pr->ops) fl += 2.0 * kop_touched_fraction(rev[i]) * kop_flops_per_amp(rev[i]);
+    // consecutive double-float segments pass psi and lambda as hi/lo float
+    // pairs; the sweep reads and leaves float64 states
+    const unsigned fmt = (j > 0 ? 1u : 0u) | (j + 1 < progs.size() ? 2u : 0u);
     LQS_TRY(jit_launch_adjoint(pr->entry, pr->P, r, sv, lam, partial + off * grid, grid, 4.0 * (double)sv->bytes(),
-                               fl * (double)sv->N(), pname.c_str()));
+                               fl * (double)sv->N(), pname.c_str(), fmt));
     off += pr->gops.size();
     slot_op.insert(slot_op.end(), pr->gops.begin(), pr->gops.end());
   }
@@ -1002,10 +1008,24 @@ int run_adjoint_compiled(SV* sv, const std::vector<KOp>& rev, void* lam, int ari
   return run_adjoint_compiled_t<ArDF>(sv, rev, lam, arith, slot_op, partial, grid);
 }
 
-int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {
-  if (sv->dtype == LQS_C64) return launch_fused_reg_t<ArF32>(sv, ops, seg, k, b, arith);
-  if (arith == LQS_ARITH_F64) return launch_fused_reg_t<ArF64>(sv, ops, seg, k, b, arith);
-  return launch_fused_reg_t<ArDF>(sv, ops, seg, k, b, arith);
+int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith,
+                     unsigned fmt) {
+  if (sv->dtype == LQS_C64) return launch_fused_reg_t<ArF32>(sv, ops, seg, k, b, arith, fmt);
+  if (arith == LQS_ARITH_F64) return launch_fused_reg_t<ArF64>(sv, ops, seg, k, b, arith, fmt);
+  return launch_fused_reg_t<ArDF>(sv, ops, seg, k, b, arith, fmt);
+}
+
+// True when a double-float forward segment runs as exactly one compiled
+// kernel right now: launch_segment's routing (more than one op, the
+// register tile's shape), a program that fits one kernel, and its kernel
+// compiled.  Only such launches can hand hi/lo pairs to one another.
+bool seg_split_capable(const SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith) {
+  if (sv->dtype != LQS_C128 || arith == LQS_ARITH_F64 || seg.ops.size() < 2) return false;
+  if (k != reg_tile_qubits(sv->dtype) || !jit_enabled_for(sv->n)) return false;
+  static thread_local TileProg<ArDF> P;
+  init_prog(P, sv->n, seg.qmask, k, b);
+  if (build_reg_prog(P, ops, seg, JitR<ArDF>::r, nullptr, true) != LQS_OK) return false;  // launched split in two
+  return jit_ready(P, JitR<ArDF>::r, sv);
 }
 
 }  // namespace lqs

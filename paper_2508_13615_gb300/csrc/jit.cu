@@ -80,6 +80,17 @@ constexpr int kMaxGradSlotsJit = 128;  // gradient slots per compiled adjoint se
 // updates between renormalisations, and 2-5x that at 64-128.
 constexpr int kRenormEvery = 16;
 
+// A forward program's unit-row forms leave every amplitude scaled by 1/g, the
+// product of their factors.  The scalar commutes with every op, so it is
+// folded into the constant of the first merged diagonal run that multiplies
+// every amplitude (no controls); without one the store scales by g.  The
+// generator and the parameter block both take the run this picks.
+int gscale_sink(const TOp* ops, int nops) {
+  for (int i = 0; i < nops; ++i)
+    if (ops[i].kind == K_DPROD && ops[i].lcmask == 0 && ops[i].ecmask == 0) return i;
+  return -1;
+}
+
 std::string hex(uint64_t x) {
   char b[32];
   std::snprintf(b, sizeof b, "0x%llxull", (unsigned long long)x);
@@ -146,6 +157,11 @@ class SegGen {
   }
 
   int nthreads() const { return 1 << (k_ - r_); }
+  // Double-float segments take the states' format as a launch-time argument:
+  // bit 0, the tiles hold hi/lo float pairs (written by the previous compiled
+  // segment of the same call) instead of float64; bit 1, leave hi/lo pairs
+  // for the next one.  Both skip the float64 conversions.
+  bool split_io() const { return aname_ == std::string("lqs::ArDF"); }
   void flush_pending(bool all);
   // runs f once per state, with V() naming that state's variables
   template <class F>
@@ -554,12 +570,22 @@ void SegGen::emit_store() {
   }
   each([&]() {
     o_ << "    { S* out = " << (pfx_[0] == 'v' ? "psi" : "lam") << " + base + st_t;\n";
+    std::vector<std::string> offs(R_);
     for (int e = 0; e < R_; ++e) {
-      std::string off;
       for (int m = 0; m < r_; ++m)
-        if ((e >> m) & 1) off += (off.empty() ? "" : " + ") + ("st_" + std::to_string(m));
-      o_ << "      out[" << (off.empty() ? std::string("0") : off) << "] = A::store(" << V(e) << ");\n";
+        if ((e >> m) & 1) offs[e] += (offs[e].empty() ? "" : " + ") + ("st_" + std::to_string(m));
+      if (offs[e].empty()) offs[e] = "0";
     }
+    if (split_io()) {  // the next segment of this call reads hi/lo pairs: renormalise, no conversion
+      o_ << "      if (fmt & 2u) {\n        W* wo = reinterpret_cast<W*>(out);\n";
+      for (int e = 0; e < R_; ++e)
+        o_ << "        lqs::jit::renorm<A>(" << V(e) << ");\n        lqs::st_w(&wo[" << offs[e] << "], " << V(e)
+           << ");\n";
+      o_ << "      } else {\n";
+    }
+    for (int e = 0; e < R_; ++e)
+      o_ << (split_io() ? "  " : "") << "      out[" << offs[e] << "] = A::store(" << V(e) << ");\n";
+    if (split_io()) o_ << "      }\n";
     o_ << "    }\n";
   });
 }
@@ -840,6 +866,15 @@ bool SegGen::emit_op(const TOp& t) {
           if (!((e >> m) & 1) && qual(e)) std::swap(vm_[e], vm_[e | (1 << m)]);
         return true;
       }
+      if (t.kind == K_DENSE1R && !adj_ && t.special == 3) {  // Hadamard pattern: g (a + b, a - b)
+        if (!p.empty() || regc) return fail("internal: controlled op marked orthogonal");
+        ++nu_;  // its g joins the product; its form bit is unused
+        each([&]() {
+          for (int e = 0; e < R_; ++e)
+            if (!((e >> m) & 1)) o_ << "    lqs::jit::u1h<A>(" << V(e) << ", " << V(e | (1 << m)) << ");\n";
+        });
+        return true;
+      }
       if (t.kind == K_DENSE1R && !adj_ && (t.special == 1 || t.special == 2)) {
         // g times a matrix with a unit entry per row; the form (pivot m00 or
         // m10) is a launch-time bit, so angles do not change the kernel
@@ -998,7 +1033,7 @@ bool SegGen::emit_op(const TOp& t) {
 
 const char* kSkeletonHead = R"(
 extern "C" __global__ void __launch_bounds__(@NTH@, @MINB@)
-@NAME@(A::S* __restrict__ psi, @LAMP@const __grid_constant__ SegArgs P, @PARTP@int* status) {
+@NAME@(A::S* __restrict__ psi, @LAMP@const __grid_constant__ SegArgs P, @PARTP@int* status@FMTP@) {
   typedef A::S S;
   typedef A::W W;
   typedef A::C C;
@@ -1105,9 +1140,17 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     o_ << "    W";
     for (int e = 0; e < R_; ++e) o_ << (e ? ", " : " ") << pfx_ << e;
     o_ << ";\n";
+    if (split_io()) {  // the previous segment of this call left hi/lo pairs
+      o_ << "    if (fmt & 1u) {\n";
+      for (int e = 0; e < R_; ++e)
+        o_ << "      " << pfx_ << e << " = lqs::ld_w(reinterpret_cast<const W*>(" << (pfx_[0] == 'v' ? "S0" : "S0L")
+           << " + (jt + " << hex32(je(e)) << ")));\n";
+      o_ << "    } else {\n";
+    }
     for (int e = 0; e < R_; ++e)
-      o_ << "    " << pfx_ << e << " = A::load(" << (pfx_[0] == 'v' ? "S0" : "S0L") << "[jt + " << hex32(je(e))
-         << "]);\n";
+      o_ << (split_io() ? "  " : "") << "    " << pfx_ << e << " = A::load(" << (pfx_[0] == 'v' ? "S0" : "S0L")
+         << "[jt + " << hex32(je(e)) << "]);\n";
+    if (split_io()) o_ << "    }\n";
   });
   if (logical != through) {
     set_layout(logical);
@@ -1167,7 +1210,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     }
   }
   flush_pending(true);
-  if (nu_) {
+  if (nu_ && (adj_ || gscale_sink(ops, nops) < 0)) {
     o_ << "    // the product of the unit-row forms' factors\n";
     for (int e = 0; e < R_; ++e)
       o_ << "    " << V(e) << " = lqs::jit::Lz<A>::rscale(lqs::jit::Re<A>::get(P.gscale), " << V(e) << ");\n";
@@ -1199,6 +1242,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   head = replace_all(head, "@MINB@", std::to_string(minb));
   head = replace_all(head, "@LAMP@", adj_ ? "A::S* __restrict__ lam, " : "");
   head = replace_all(head, "@PARTP@", adj_ ? "double* partial, " : "");
+  head = replace_all(head, "@FMTP@", ", const unsigned fmt");
   head = replace_all(head, "@NT@", std::to_string(1u << k_) + "u");
   head = replace_all(head, "@NIN@", adj_ ? "2u" : "1u");
   head = replace_all(head, "@NSTATES@", adj_ ? "2u" : "1u");
@@ -1610,9 +1654,18 @@ static int entry_function(Entry* e, int dev, size_t smem, int threads, CUfunctio
 }
 
 template <class A> struct CoefRe;
-template <> struct CoefRe<ArF32> { static double get(const float2& c) { return c.x; } };
-template <> struct CoefRe<ArF64> { static double get(const double2& c) { return c.x; } };
-template <> struct CoefRe<ArDF> { static double get(const DFK& c) { return (double)c.re.h + (double)c.re.l; } };
+template <> struct CoefRe<ArF32> {
+  static double get(const float2& c) { return c.x; }
+  static double im(const float2& c) { return c.y; }
+};
+template <> struct CoefRe<ArF64> {
+  static double get(const double2& c) { return c.x; }
+  static double im(const double2& c) { return c.y; }
+};
+template <> struct CoefRe<ArDF> {
+  static double get(const DFK& c) { return (double)c.re.h + (double)c.re.l; }
+  static double im(const DFK& c) { return (double)c.im.h + (double)c.im.l; }
+};
 
 static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -1630,7 +1683,7 @@ static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
   int nu = 0;
   for (int i = 0; forward && i < P.nops; ++i) {
     const TOp& t = P.op[i];
-    if (t.kind != K_DENSE1R || (t.special != 1 && t.special != 2)) continue;
+    if (t.kind != K_DENSE1R || (t.special != 1 && t.special != 2 && t.special != 3)) continue;
     const double m00 = CoefRe<A>::get(coef[t.coef]), m01 = CoefRe<A>::get(coef[t.coef + 1]);
     const double m10 = CoefRe<A>::get(coef[t.coef + 2]), m11 = CoefRe<A>::get(coef[t.coef + 3]);
     const bool form_b = std::fabs(m01) > std::fabs(m00);
@@ -1654,6 +1707,11 @@ static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
   const size_t end = nu ? uoff + usel.size() * sizeof(uint32_t) : goff;
   std::vector<unsigned char> args(round_up(end, 16), 0);
   std::memcpy(args.data(), &P.g, sizeof(TileGeom));
+  const int sink = forward && nu ? gscale_sink(P.op, P.nops) : -1;
+  if (sink >= 0) {
+    C& c0 = coef[P.op[sink].coef];
+    c0 = A::cconst(CoefRe<A>::get(c0) * gprod, CoefRe<A>::im(c0) * gprod);
+  }
   if (P.ncoef) std::memcpy(args.data() + off, coef.data(), (size_t)P.ncoef * sizeof(C));
   if (nu) {
     const C gc = A::cconst(gprod, 0.0);
@@ -1664,14 +1722,19 @@ static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
 }
 
 template <class A>
-int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, const char* prof_name,
-               bool* launched) {
-  *launched = false;
-  if (!jit_enabled_for(sv->n)) return LQS_OK;
+bool jit_ready(const TileProg<A>& P, int r, const SV* sv) {
+  if (!jit_enabled_for(sv->n) || sv->device < 0 || sv->device >= kJitMaxDevices) return false;
   Entry* e = entry_for(P, r, false, false, nullptr);
-  if (!e || e->state != 1) return LQS_OK;
+  return e && e->state == 1;
+}
+
+template <class A>
+int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, const char* prof_name,
+               bool* launched, unsigned fmt) {
+  *launched = false;
+  if (!jit_ready(P, r, sv)) return LQS_OK;
+  Entry* e = entry_for(P, r, false, false, nullptr);
   const int dev = sv->device;
-  if (dev < 0 || dev >= kJitMaxDevices) return LQS_OK;
   const int threads = 1 << (P.g.k - r);
   const size_t smem = 3 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;  // incoming tile, two exchange buffers
   CUfunction fn;
@@ -1680,7 +1743,7 @@ int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, 
   std::vector<unsigned char> args = seg_args(P, true);
   void* psi = sv->d;
   int* status = sv->d_status;
-  void* kp[] = {&psi, args.data(), &status};
+  void* kp[] = {&psi, args.data(), &status, &fmt};
   const uint64_t grid = std::min<uint64_t>(P.g.ntiles, (uint64_t)std::max(sv->sms, 1) * per_sm);
   ProfScope ps(sv->stream, prof_name, bytes, flops);
   const CUresult rr = g_drv.launch(fn, (unsigned)grid, 1, 1, threads, 1, 1, (unsigned)smem,
@@ -1717,7 +1780,7 @@ int jit_adjoint_occupancy(void* entry, const TileProg<A>& P, int r, SV* sv, int*
 
 template <class A>
 int jit_launch_adjoint(void* entry, const TileProg<A>& P, int r, SV* sv, void* lam, double* partial, unsigned grid,
-                       double bytes, double flops, const char* prof_name) {
+                       double bytes, double flops, const char* prof_name, unsigned fmt) {
   Entry* e = static_cast<Entry*>(entry);
   if (e->state != 1) return set_error(LQS_ERR_UNSUPPORTED, "compiled adjoint segment is not available");
   const int dev = sv->device;
@@ -1730,7 +1793,7 @@ int jit_launch_adjoint(void* entry, const TileProg<A>& P, int r, SV* sv, void* l
   std::vector<unsigned char> args = seg_args(P, false);
   void* psi = sv->d;
   int* status = sv->d_status;
-  void* kp[] = {&psi, &lam, args.data(), &partial, &status};
+  void* kp[] = {&psi, &lam, args.data(), &partial, &status, &fmt};
   ProfScope ps(sv->stream, prof_name, bytes, flops);
   const CUresult rr = g_drv.launch(fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, (CUstream)sv->stream, kp, nullptr);
   if (rr != CUDA_SUCCESS) return cu_error(rr, "cuLaunchKernel(compiled adjoint segment)");
@@ -1795,9 +1858,12 @@ template int jit_source<ArDF>(const TileProg<ArDF>&, int, std::string&, std::str
 template int jit_note<ArF32>(const TileProg<ArF32>&, int, int, bool, std::vector<void*>&);
 template int jit_note<ArF64>(const TileProg<ArF64>&, int, int, bool, std::vector<void*>&);
 template int jit_note<ArDF>(const TileProg<ArDF>&, int, int, bool, std::vector<void*>&);
-template int jit_launch<ArF32>(const TileProg<ArF32>&, int, SV*, double, double, const char*, bool*);
-template int jit_launch<ArF64>(const TileProg<ArF64>&, int, SV*, double, double, const char*, bool*);
-template int jit_launch<ArDF>(const TileProg<ArDF>&, int, SV*, double, double, const char*, bool*);
+template int jit_launch<ArF32>(const TileProg<ArF32>&, int, SV*, double, double, const char*, bool*, unsigned);
+template bool jit_ready<ArF32>(const TileProg<ArF32>&, int, const SV*);
+template int jit_launch<ArF64>(const TileProg<ArF64>&, int, SV*, double, double, const char*, bool*, unsigned);
+template bool jit_ready<ArF64>(const TileProg<ArF64>&, int, const SV*);
+template int jit_launch<ArDF>(const TileProg<ArDF>&, int, SV*, double, double, const char*, bool*, unsigned);
+template bool jit_ready<ArDF>(const TileProg<ArDF>&, int, const SV*);
 template int jit_adjoint_entry<ArF32>(const TileProg<ArF32>&, int, void**, std::string*);
 template int jit_adjoint_occupancy<ArF32>(void*, const TileProg<ArF32>&, int, SV*, int*);
 template int jit_adjoint_occupancy<ArF64>(void*, const TileProg<ArF64>&, int, SV*, int*);
@@ -1805,11 +1871,11 @@ template int jit_adjoint_occupancy<ArDF>(void*, const TileProg<ArDF>&, int, SV*,
 template int jit_adjoint_entry<ArF64>(const TileProg<ArF64>&, int, void**, std::string*);
 template int jit_adjoint_entry<ArDF>(const TileProg<ArDF>&, int, void**, std::string*);
 template int jit_launch_adjoint<ArF32>(void*, const TileProg<ArF32>&, int, SV*, void*, double*, unsigned, double, double,
-                                       const char*);
+                                       const char*, unsigned);
 template int jit_launch_adjoint<ArF64>(void*, const TileProg<ArF64>&, int, SV*, void*, double*, unsigned, double, double,
-                                       const char*);
+                                       const char*, unsigned);
 template int jit_launch_adjoint<ArDF>(void*, const TileProg<ArDF>&, int, SV*, void*, double*, unsigned, double, double,
-                                      const char*);
+                                      const char*, unsigned);
 
 }  // namespace lqs
 

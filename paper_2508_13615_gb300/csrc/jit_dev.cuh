@@ -51,6 +51,14 @@ template <class A> struct Lz {
     r.y = g * x.y;
     return r;
   }
+  // x + SY y
+  template <int SY>
+  static __device__ __forceinline__ W uadd(const W& x, const W& y) {
+    W r;
+    r.x = SY > 0 ? x.x + y.x : x.x - y.x;
+    r.y = SY > 0 ? x.y + y.y : x.y - y.y;
+    return r;
+  }
 };
 template <> struct Lz<ArDF> {
   using W = DFC;
@@ -120,6 +128,19 @@ template <> struct Lz<ArDF> {
   static __device__ __forceinline__ W rscale(const DF& g, const W& x) {
     return W{raw(df_prod(x.re, g)), raw(df_prod(x.im, g))};
   }
+  // x + SY y: one TwoSum of the leading parts, the low parts and the error added
+  template <int SY>
+  static __device__ __forceinline__ DF uadd1(const DF& x, const DF& y) {
+    const float yh = SY > 0 ? y.h : -y.h, yl = SY > 0 ? y.l : -y.l;
+    const float s = fadd(x.h, yh);
+    const float bp = fsub(s, x.h);
+    const float err = fadd(fsub(x.h, fsub(s, bp)), fsub(yh, bp));
+    return DF{s, fadd(fadd(x.l, yl), err)};
+  }
+  template <int SY>
+  static __device__ __forceinline__ W uadd(const W& x, const W& y) {
+    return W{uadd1<SY>(x.re, y.re), uadd1<SY>(x.im, y.im)};
+  }
 };
 
 template <class A>
@@ -169,6 +190,15 @@ __device__ __forceinline__ void u1b(typename A::W& a, typename A::W& b, const ty
   const typename A::W x = a, y = b;
   a = Lz<A>::template uma<-SG>(y, Re<A>::get(k0), x);
   b = Lz<A>::template uma<1>(x, Re<A>::get(k1), y);
+}
+
+// The Hadamard pattern (m00 = m01 = m10 = -m11 = g): form A with k0 = k1 = 1,
+// a' = a + b and b' = a - b, sums only; g joins the product of the g's.
+template <class A>
+__device__ __forceinline__ void u1h(typename A::W& a, typename A::W& b) {
+  const typename A::W x = a, y = b;
+  a = Lz<A>::template uadd<1>(x, y);
+  b = Lz<A>::template uadd<-1>(x, y);
 }
 
 // (x0..x3) <- U x with U row-major at u[0..15]

@@ -149,11 +149,17 @@ double block_weight(const KOp& op);
 // The configuration lqs_autotune_fused chose for this circuit structure, if any.
 bool tuned_cfg(int n, int dtype, const lqs_op* ops, int n_ops, lqs_fuse_cfg* out);
 int plan_segments(int n, const std::vector<KOp>& ops, const PlanCfg& pc, std::vector<Segment>& segs);
-int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith);
+// fmt != 0 only for a segment that seg_split_capable accepted (see jit_launch).
+int launch_segment(SV* sv, const std::vector<KOp>& ops, const Segment& seg, const PlanCfg& pc, int arith,
+                   unsigned fmt = 0);
 // Register-resident tile kernel (k = reg_tile_qubits(dtype)); returns
 // LQS_ERR_UNSUPPORTED when the segment's program does not fit (split it).
 int reg_tile_qubits(int dtype);
-int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith);
+int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith,
+                     unsigned fmt = 0);
+// True when launch_segment runs this complex128 double-float segment as one
+// compiled kernel, which can read and leave hi/lo float pairs.
+bool seg_split_capable(const SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith);
 // Compiled adjoint: the reverse sweep's segments as register-tile programs
 // over psi and lambda.  reg_adjoint_available tells whether this state takes
 // it (mode, size); run_adjoint_compiled launches all segments, writing the
