@@ -107,7 +107,8 @@ class SegGen {
   // adjoint: the kernel carries psi and lambda (same layout and renamings),
   // and ops with a gradient slot (and K_GRAD partials) add Im<lambda|G|psi>.
   SegGen(int k, int b, int r, const char* aname, int amp_bytes, bool adjoint)
-      : k_(k), b_(b), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes), adj_(adjoint) {}
+      : k_(k), b_(b), r_(r), R_(1 << r), aname_(aname), sz_(amp_bytes), adj_(adjoint),
+        xpair_(adjoint && amp_bytes == 16) {}
   void set_folds(const TFold* f) { folds_ = f; }
 
   // Returns false (with a reason) for a program this generator does not take.
@@ -120,6 +121,10 @@ class SegGen {
   bool adj_;
   const char* pfx_ = "v";       // variables of the state being emitted ("v" psi, "u" lambda)
   int xb_ = 0;                  // exchange buffer of the next exchange (they alternate)
+  // complex128 adjoint: psi and lambda cross each exchange together, through
+  // the pair XA/XB or XC/XD (alternating), under one barrier
+  bool xpair_ = false;
+  int xp_ = 0;
   int next_bar_ = 1;            // next free named barrier id in this tile iteration (0 is the block barrier)
   int slot_[4] = {0, 0, 0, 0};  // register slot m -> local position
   int thr_[16] = {0};           // thread bit m -> local position
@@ -136,7 +141,7 @@ class SegGen {
   // writing and the warp reading each buffer position, and its barrier's
   // groups (warps agreeing on the tid bits of gmask; 0 = the whole block).
   struct XRec {
-    int buf;
+    uint32_t bufs;  // buffers written and read by the exchange (bit per buffer)
     bool writes;  // its writes are not yet ordered before everything (no block barrier after them)
     std::vector<uint8_t> wown, rown;
     uint32_t gmask;
@@ -409,7 +414,7 @@ bool SegGen::exchange_safe(int buf, const std::vector<uint8_t>& wown) const {
   const int nw = nthreads() / 32;
   for (size_t j = 0; j < xhist_.size(); ++j) {
     const XRec& h = xhist_[j];
-    if (h.buf != buf) continue;
+    if (!((h.bufs >> buf) & 1u)) continue;
     std::vector<std::vector<char>> rw((size_t)nw), rr((size_t)nw);
     for (int v = 0; v < nw; ++v) {
       if (h.writes) rw[(size_t)v] = reach(v, j);
@@ -480,6 +485,58 @@ void SegGen::emit_layout(const TOp& t) {
   const std::vector<uint8_t> rown = owners(xs);
   std::copy(saved_slot, saved_slot + 4, slot_);
   std::copy(saved_thr, saved_thr + 16, thr_);
+  if (xpair_) {
+    // both states: writes into the pair, one barrier, reads from the pair.
+    // The pair used two exchanges ago was last read before the previous
+    // exchange's barrier.
+    const int bp = 2 * xp_, bl = 2 * xp_ + 1;
+    const char* XP = xp_ ? "XC" : "XA";
+    const char* XL = xp_ ? "XD" : "XB";
+    xp_ ^= 1;
+    bool unsafe = !exchange_safe(bp, wown) || !exchange_safe(bl, wown);
+    if (F)
+      for (const XRec& h : xhist_) unsafe = unsafe || ((h.bufs >> bp) & 1u) || ((h.bufs >> bl) & 1u);
+    if (unsafe) {
+      o_ << "    __syncthreads();  // earlier users of these buffers are not ordered before these writes\n";
+      next_bar_ = 1;
+      xhist_.clear();
+    }
+    uint32_t gmask = 0;
+    std::string bar;
+    if (F) {
+      bar = "__syncthreads();";
+      next_bar_ = 1;
+    } else {
+      bar = barrier_for(t.ecmask, &gmask);
+    }
+    if (!gmask) xhist_.clear();
+    xhist_.push_back(XRec{(1u << bp) | (1u << bl), gmask != 0, wown, rown, gmask});
+    o_ << "    { const uint32_t sj = " << jo << ";\n";
+    for (const char* pf : {"v", "u"}) {
+      pfx_ = pf;
+      for (int e = 0; e < R_; ++e) {
+        const uint32_t pos = F ? fold_lin(*F, old_je[e]) : old_je[e];
+        o_ << "      lqs::st_w(&" << (pf[0] == 'v' ? XP : XL) << "[sj ^ " << hex32(host_xswz(pos, sz_, xs)) << "], "
+           << V(e) << ");\n";
+      }
+    }
+    pfx_ = "v";
+    o_ << "    }\n    " << bar << "\n";
+    set_layout(t.ecmask);  // validated by the caller
+    o_ << "    jt = " << jt_expr() << ";\n";
+    o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
+    for (const char* pf : {"v", "u"})
+      for (int e = 0; e < R_; ++e)
+        o_ << "      " << pf << e << " = lqs::ld_w(&" << (pf[0] == 'v' ? XP : XL) << "[sj ^ "
+           << hex32(host_xswz(je(e), sz_, xs)) << "]);\n";
+    o_ << "    }\n";
+    for (int e = 0; e < R_; ++e) vm_[e] = e;
+    if (t.e0 != t.ecmask) {
+      set_layout(t.e0);
+      o_ << "    jt = " << jt_expr() << ";\n";
+    }
+    return;
+  }
   each([&]() {
     const int xi = xb_;
     const char* X = xb_ ? "XB" : "XA";
@@ -488,7 +545,7 @@ void SegGen::emit_layout(const TOp& t) {
     std::copy(saved_thr, saved_thr + 16, thr_);
     bool unsafe = !exchange_safe(xi, wown);
     if (F)  // the write positions move with each tile's outside bits: no earlier user of the buffer may be pending
-      for (const XRec& h : xhist_) unsafe = unsafe || h.buf == xi;
+      for (const XRec& h : xhist_) unsafe = unsafe || ((h.bufs >> xi) & 1u);
     if (unsafe) {
       // a warp of another group may still use this buffer's positions from
       // an earlier exchange: wait for the whole block first
@@ -505,7 +562,7 @@ void SegGen::emit_layout(const TOp& t) {
       bar = barrier_for(t.ecmask, &gmask);
     }
     if (!gmask) xhist_.clear();
-    xhist_.push_back(XRec{xi, gmask != 0, wown, rown, gmask});
+    xhist_.push_back(XRec{1u << xi, gmask != 0, wown, rown, gmask});
     if (adj_) o_ << "    { const uint32_t sj = " << jo << ";\n";
     else o_ << "    { const uint32_t sj = " << swz_expr(wj, xs) << ";\n";
     for (int e = 0; e < R_; ++e) {
@@ -1043,11 +1100,15 @@ extern "C" __global__ void __launch_bounds__(@NTH@, @MINB@)
   S* S0L = S0 + @NT@;                      // incoming lambda tiles (adjoint only)
   W* XA = reinterpret_cast<W*>(S0 + @NT@ * @NIN@);  // layout exchanges alternate between XA and XB
   W* XB = XA + @NT@;
-  double* wacc = reinterpret_cast<double*>(XB + @NT@);  // adjoint: per-warp gradient slots
+  W* XC = XB + @NT@;  // complex128 adjoint: the second pair of exchange buffers
+  W* XD = XC + @NT@;
+  double* wacc = reinterpret_cast<double*>(XA + @NT@ * @NX@);  // adjoint: per-warp gradient slots
   uint64_t* bar = reinterpret_cast<uint64_t*>(wacc + @NWACC@);
   const uint32_t tid = threadIdx.x;
   const uint32_t warp = tid >> 5;
   (void)S0L;
+  (void)XC;
+  (void)XD;
   (void)warp;
   for (uint32_t i = tid; i < @NWACC@; i += blockDim.x) wacc[i] = 0.0;
   uint64_t t = blockIdx.x;
@@ -1245,6 +1306,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   head = replace_all(head, "@FMTP@", ", const unsigned fmt");
   head = replace_all(head, "@NT@", std::to_string(1u << k_) + "u");
   head = replace_all(head, "@NIN@", adj_ ? "2u" : "1u");
+  head = replace_all(head, "@NX@", xpair_ ? "4u" : "2u");
   head = replace_all(head, "@NSTATES@", adj_ ? "2u" : "1u");
   head = replace_all(head, "@NWACC@", std::to_string(adj_ ? nwarps * kMaxGradSlotsJit : 0) + "u");
   head = replace_all(head, "@LAMCOPY0@",
@@ -1765,7 +1827,8 @@ int jit_adjoint_entry(const TileProg<A>& P, int r, void** entry, std::string* wh
 
 size_t jit_adjoint_smem(int k, int r, size_t amp_bytes) {
   const int warps = (1 << (k - r)) / 32;
-  return 4 * (amp_bytes << k) + sizeof(double) * warps * kMaxGradSlotsJit + 16;
+  const size_t tiles = amp_bytes == 16 ? 6 : 4;  // incoming psi and lambda, two (complex128: four) exchange buffers
+  return tiles * (amp_bytes << k) + sizeof(double) * warps * kMaxGradSlotsJit + 16;
 }
 
 template <class A>

@@ -218,7 +218,7 @@ def _unordered_accesses(src):
             sj = [ev(m.group(1), jt=jt[t], **{k: v[t] for k, v in named.items()}) for t in range(nth)]
             cur = None
             continue
-        m = re.search(r"(st_w|ld_w)\(&(X[AB])\[sj \^ (0x[0-9a-f]+)u\]", s)
+        m = re.search(r"(st_w|ld_w)\(&(X[ABCD])\[sj \^ (0x[0-9a-f]+)u\]", s)
         if m and sj is not None:
             wr, buf, c = m.group(1) == "st_w", m.group(2), int(m.group(3), 16)
             if cur is None or cur[1] != buf or cur[2] != wr:
