@@ -1144,7 +1144,7 @@ const char* kSkeletonTail = R"(  }
 const char* kGradOut = R"(  __syncthreads();
   for (int s = tid; s < @NGRAD@; s += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < @NWARPS@; ++w) v += wacc[w * @SLOTS@ + s];
+    for (int w = 0; w < @NWARPS@; ++w) v += lqs::jit::slot_get<A>(wacc + w * @SLOTS@ + s);
     partial[(size_t)s * gridDim.x + blockIdx.x] = v;
   }
 )";

@@ -348,14 +348,28 @@ __device__ __forceinline__ void wadd(float& acc, float w, bool neg) { acc = neg 
 __device__ __forceinline__ DAcc gneg(const DAcc& a, bool neg) { return neg ? DAcc{-a.s, -a.e} : a; }
 __device__ __forceinline__ float gneg(float a, bool neg) { return neg ? -a : a; }
 
-// Warp sum of a partial, added in float64 by lane 0 to the warp's slot.  All
-// 32 lanes must call it.
+// Per-warp partial-sum slots.  Double-float kernels keep each 8-byte slot as
+// a double-float pair and add to it with float32 operations (float64 adds run
+// on a far narrower pipe); the slot is read as a float64 once, after the tile
+// loop.  Float32 kernels add in float64.
+__device__ __forceinline__ void slot_add(double* slot, const DF& v) {
+  DF* d = reinterpret_cast<DF*>(slot);
+  *d = df_add(*d, v);
+}
+template <class A>
+__device__ __forceinline__ double slot_get(const double* slot) {
+  if constexpr (sizeof(typename GAcc<A>::T) == sizeof(float)) return *slot;
+  else return df2d(*reinterpret_cast<const DF*>(slot));
+}
+
+// Warp sum of a partial, added by lane 0 to the warp's slot.  All 32 lanes
+// must call it.
 __device__ __forceinline__ void gflush(DAcc a, double* slot) {
   DF v = df_norm(a);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
     v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)});
-  if ((threadIdx.x & 31u) == 0) *slot += df2d(v);
+  if ((threadIdx.x & 31u) == 0) slot_add(slot, v);
 }
 __device__ __forceinline__ void gflush(float a, double* slot) {
 #pragma unroll
@@ -386,7 +400,7 @@ __device__ __forceinline__ void gflush4(const DAcc& a0, const DAcc& a1, const DA
   k = df_add(k, shfl_df(k, 2));
   k = df_add(k, shfl_df(k, 1));
   double* s = u16 ? (u8 ? s3 : s2) : (u8 ? s1 : s0);
-  if ((lane & 7u) == 0 && s) *s += df2d(k);
+  if ((lane & 7u) == 0 && s) slot_add(s, k);
 }
 __device__ __forceinline__ void gflush4(float a0, float a1, float a2, float a3, double* s0, double* s1, double* s2,
                                         double* s3) {
@@ -429,7 +443,7 @@ __device__ __forceinline__ float wht(float v) {
 }
 // slot += (neg ? -w : w) where `cond` holds (one lane per slot).
 __device__ __forceinline__ void gput(const DF& w, bool cond, bool neg, double* slot) {
-  if (cond) *slot += neg ? -df2d(w) : df2d(w);
+  if (cond) slot_add(slot, neg ? df_neg(w) : w);
 }
 __device__ __forceinline__ void gput(float w, bool cond, bool neg, double* slot) {
   if (cond) *slot += neg ? -(double)w : (double)w;

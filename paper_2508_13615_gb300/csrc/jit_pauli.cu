@@ -307,8 +307,8 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
        "  __syncthreads();\n"
     << "  for (int w = tid; w < " << nw << "; w += blockDim.x) {\n"
        "    double v = 0.0;\n"
-       "    for (int q = 0; q < 8; ++q) v += wacc[q * "
-    << nw << " + w];\n"
+       "    for (int q = 0; q < 8; ++q) v += lqs::jit::slot_get<A>(wacc + q * "
+    << nw << " + w);\n"
        "    partial[(size_t)w * pstride + blockIdx.x] = v;\n  }\n}\n";
   return s.str();
 }
