@@ -20,6 +20,7 @@
 // bulk asynchronous copies; the result is written through the second buffer
 // and stored by bulk copies.
 #include <algorithm>
+#include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
@@ -946,7 +947,8 @@ static int adj_prepare_t(int n, int dtype, const std::vector<KOp>& rev, std::vec
 
 template <class A>
 static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam, int arith,
-                                  std::vector<int>& slot_op, double** partial_out, int* grid_out) {
+                                  std::vector<int>& slot_op, std::vector<double>& slot_scale, double** partial_out,
+                                  int* grid_out) {
   int r, tb;
   adj_shape(sv->dtype, &r, &tb);
   const int n = sv->n, k = r + tb;
@@ -954,6 +956,16 @@ static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam
   LQS_TRY(adj_prepare_t<A>(n, sv->dtype, rev, progs, nullptr, false));
   size_t nslots = 0;
   for (auto& pr : progs) nslots += pr->gops.size();
+  // unit-row un-applies scale psi and lambda by up to 1 / (product of the
+  // segment's pivots); a product below 2^-40 (angles within about 1e-12**(1/m)
+  // of pi) would take them out of float32 range, so the interpreter runs it
+  std::vector<std::vector<double>> scales(progs.size());
+  for (size_t j = 0; j < progs.size(); ++j) {
+    double gprod = 1.0;
+    jit_adjoint_scales(progs[j]->P, scales[j], &gprod);
+    if (!(std::fabs(gprod) >= 0x1p-40))
+      return set_error(LQS_ERR_UNSUPPORTED, "compiled adjoint: a segment's rotations are too close to pi");
+  }
   // one grid for all segments (the partial sums share a layout): as many
   // CTAs as the least occupant kernel keeps resident
   int per_sm = 8;
@@ -981,6 +993,7 @@ static int run_adjoint_compiled_t(SV* sv, const std::vector<KOp>& rev, void* lam
                                fl * (double)sv->N(), pname.c_str(), fmt));
     off += pr->gops.size();
     slot_op.insert(slot_op.end(), pr->gops.begin(), pr->gops.end());
+    for (size_t q = 0; q < pr->gops.size(); ++q) slot_scale.push_back(q < scales[j].size() ? scales[j][q] : 1.0);
   }
   *partial_out = partial;
   *grid_out = (int)grid;
@@ -1001,11 +1014,14 @@ int adjoint_precompile(int n, int dtype, int arith, const std::vector<KOp>& rev,
 }
 
 int run_adjoint_compiled(SV* sv, const std::vector<KOp>& rev, void* lam, int arith, std::vector<int>& slot_op,
-                         double** partial, int* grid) {
+                         std::vector<double>& slot_scale, double** partial, int* grid) {
   slot_op.clear();
-  if (sv->dtype == LQS_C64) return run_adjoint_compiled_t<ArF32>(sv, rev, lam, arith, slot_op, partial, grid);
-  if (arith == LQS_ARITH_F64) return run_adjoint_compiled_t<ArF64>(sv, rev, lam, arith, slot_op, partial, grid);
-  return run_adjoint_compiled_t<ArDF>(sv, rev, lam, arith, slot_op, partial, grid);
+  slot_scale.clear();
+  if (sv->dtype == LQS_C64)
+    return run_adjoint_compiled_t<ArF32>(sv, rev, lam, arith, slot_op, slot_scale, partial, grid);
+  if (arith == LQS_ARITH_F64)
+    return run_adjoint_compiled_t<ArF64>(sv, rev, lam, arith, slot_op, slot_scale, partial, grid);
+  return run_adjoint_compiled_t<ArDF>(sv, rev, lam, arith, slot_op, slot_scale, partial, grid);
 }
 
 int launch_fused_reg(SV* sv, const std::vector<KOp>& ops, const Segment& seg, int k, int b, int arith,

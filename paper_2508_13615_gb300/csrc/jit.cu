@@ -36,6 +36,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <type_traits>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -167,6 +168,12 @@ class SegGen {
   // segment of the same call) instead of float64; bit 1, leave hi/lo pairs
   // for the next one.  Both skip the float64 conversions.
   bool split_io() const { return aname_ == std::string("lqs::ArDF"); }
+  // Double-float adjoint sweeps un-apply orthogonal real 2x2 ops (RY, H) in
+  // the unit-row form too, always pivoting on m00 (one form, no launch-time
+  // bit): both states grow by 1/m00 per op, which the host takes out of the
+  // gradient partials (seg_scales) and folds into a diagonal run or a final
+  // scale; launches whose product of m00's is too small run elsewhere.
+  bool unit_adj() const { return adj_ && aname_ == std::string("lqs::ArDF"); }
   void flush_pending(bool all);
   // runs f once per state, with V() naming that state's variables
   template <class F>
@@ -923,6 +930,21 @@ bool SegGen::emit_op(const TOp& t) {
           if (!((e >> m) & 1) && qual(e)) std::swap(vm_[e], vm_[e | (1 << m)]);
         return true;
       }
+      if (t.kind == K_DENSE1R && unit_adj() && t.special >= 1 && t.special <= 3) {
+        if (!p.empty() || regc) return fail("internal: controlled op marked orthogonal");
+        ++nu_;
+        const int sg = t.special == 1 ? 1 : -1;
+        each([&]() {
+          for (int e = 0; e < R_; ++e) {
+            if ((e >> m) & 1) continue;
+            if (t.special == 3) o_ << "    lqs::jit::u1h<A>(" << V(e) << ", " << V(e | (1 << m)) << ");\n";
+            else
+              o_ << "    lqs::jit::u1a<A, " << sg << ">(" << V(e) << ", " << V(e | (1 << m)) << ", " << cref(c) << ", "
+                 << cref(c + 1) << ");\n";
+          }
+        });
+        return true;
+      }
       if (t.kind == K_DENSE1R && !adj_ && t.special == 3) {  // Hadamard pattern: g (a + b, a - b)
         if (!p.empty() || regc) return fail("internal: controlled op marked orthogonal");
         ++nu_;  // its g joins the product; its form bit is unused
@@ -1271,10 +1293,12 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     }
   }
   flush_pending(true);
-  if (nu_ && (adj_ || gscale_sink(ops, nops) < 0)) {
+  if (nu_ && gscale_sink(ops, nops) < 0) {
     o_ << "    // the product of the unit-row forms' factors\n";
-    for (int e = 0; e < R_; ++e)
-      o_ << "    " << V(e) << " = lqs::jit::Lz<A>::rscale(lqs::jit::Re<A>::get(P.gscale), " << V(e) << ");\n";
+    each([&]() {
+      for (int e = 0; e < R_; ++e)
+        o_ << "    " << V(e) << " = lqs::jit::Lz<A>::rscale(lqs::jit::Re<A>::get(P.gscale), " << V(e) << ");\n";
+    });
   }
   emit_store();  // natural order, or a layout that keeps sectors on lanes
   const std::string body = o_.str();
@@ -1736,6 +1760,13 @@ static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // unit-row form (jit_dev.cuh u1a / u1b): k0, k1 in the op's first two
 // coefficients, then the product of their factors g and one form bit per op,
 // numbered in op order as the generator numbers them.
+// Whether a program's orthogonal real 2x2 ops run in unit-row form: every
+// forward program, and double-float adjoint programs (one form, pivot m00).
+template <class A>
+static bool unit_rows(bool forward) {
+  return forward || std::is_same<A, ArDF>::value;
+}
+
 template <class A>
 static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
   using C = typename A::C;
@@ -1743,12 +1774,12 @@ static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
   std::vector<uint32_t> usel;
   double gprod = 1.0;
   int nu = 0;
-  for (int i = 0; forward && i < P.nops; ++i) {
+  for (int i = 0; unit_rows<A>(forward) && i < P.nops; ++i) {
     const TOp& t = P.op[i];
     if (t.kind != K_DENSE1R || (t.special != 1 && t.special != 2 && t.special != 3)) continue;
     const double m00 = CoefRe<A>::get(coef[t.coef]), m01 = CoefRe<A>::get(coef[t.coef + 1]);
     const double m10 = CoefRe<A>::get(coef[t.coef + 2]), m11 = CoefRe<A>::get(coef[t.coef + 3]);
-    const bool form_b = std::fabs(m01) > std::fabs(m00);
+    const bool form_b = forward && std::fabs(m01) > std::fabs(m00);
     const double g = form_b ? m10 : m00;
     double k0 = 0.0, k1 = 0.0;
     if (g != 0.0) {
@@ -1769,7 +1800,7 @@ static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
   const size_t end = nu ? uoff + usel.size() * sizeof(uint32_t) : goff;
   std::vector<unsigned char> args(round_up(end, 16), 0);
   std::memcpy(args.data(), &P.g, sizeof(TileGeom));
-  const int sink = forward && nu ? gscale_sink(P.op, P.nops) : -1;
+  const int sink = nu ? gscale_sink(P.op, P.nops) : -1;
   if (sink >= 0) {
     C& c0 = coef[P.op[sink].coef];
     c0 = A::cconst(CoefRe<A>::get(c0) * gprod, CoefRe<A>::im(c0) * gprod);
@@ -1781,6 +1812,34 @@ static std::vector<unsigned char> seg_args(const TileProg<A>& P, bool forward) {
     std::memcpy(args.data() + uoff, usel.data(), usel.size() * sizeof(uint32_t));
   }
   return args;
+}
+
+template <class A>
+void jit_adjoint_scales(const TileProg<A>& P, std::vector<double>& scale, double* gprod_out) {
+  scale.assign((size_t)std::max(P.ngrad, 0), 1.0);
+  *gprod_out = 1.0;
+  if (!unit_rows<A>(false)) return;
+  std::vector<double> g((size_t)P.nops, 0.0);  // the pivot m00 of each unit-row op
+  double gprod = 1.0;
+  int nu = 0;
+  for (int i = 0; i < P.nops; ++i) {
+    const TOp& t = P.op[i];
+    if (t.kind != K_DENSE1R || (t.special != 1 && t.special != 2 && t.special != 3)) continue;
+    g[(size_t)i] = CoefRe<A>::get(P.coef[t.coef]);
+    gprod *= g[(size_t)i];
+    ++nu;
+  }
+  const int sink = nu ? gscale_sink(P.op, P.nops) : -1;
+  // psi and lambda in registers are S times their values; a partial is
+  // taken before its op is un-applied and comes out scaled by S^2
+  double S = 1.0;
+  for (int i = 0; i < P.nops; ++i) {
+    const TOp& t = P.op[i];
+    if (t.gslot >= 0 && t.gslot < P.ngrad) scale[(size_t)t.gslot] = 1.0 / (S * S);
+    if (g[(size_t)i] != 0.0) S /= g[(size_t)i];
+    if (i == sink) S *= gprod;
+  }
+  *gprod_out = gprod;
 }
 
 template <class A>
@@ -1923,10 +1982,13 @@ template int jit_note<ArF64>(const TileProg<ArF64>&, int, int, bool, std::vector
 template int jit_note<ArDF>(const TileProg<ArDF>&, int, int, bool, std::vector<void*>&);
 template int jit_launch<ArF32>(const TileProg<ArF32>&, int, SV*, double, double, const char*, bool*, unsigned);
 template bool jit_ready<ArF32>(const TileProg<ArF32>&, int, const SV*);
+template void jit_adjoint_scales<ArF32>(const TileProg<ArF32>&, std::vector<double>&, double*);
 template int jit_launch<ArF64>(const TileProg<ArF64>&, int, SV*, double, double, const char*, bool*, unsigned);
 template bool jit_ready<ArF64>(const TileProg<ArF64>&, int, const SV*);
+template void jit_adjoint_scales<ArF64>(const TileProg<ArF64>&, std::vector<double>&, double*);
 template int jit_launch<ArDF>(const TileProg<ArDF>&, int, SV*, double, double, const char*, bool*, unsigned);
 template bool jit_ready<ArDF>(const TileProg<ArDF>&, int, const SV*);
+template void jit_adjoint_scales<ArDF>(const TileProg<ArDF>&, std::vector<double>&, double*);
 template int jit_adjoint_entry<ArF32>(const TileProg<ArF32>&, int, void**, std::string*);
 template int jit_adjoint_occupancy<ArF32>(void*, const TileProg<ArF32>&, int, SV*, int*);
 template int jit_adjoint_occupancy<ArF64>(void*, const TileProg<ArF64>&, int, SV*, int*);

@@ -163,11 +163,13 @@ bool seg_split_capable(const SV* sv, const std::vector<KOp>& ops, const Segment&
 // Compiled adjoint: the reverse sweep's segments as register-tile programs
 // over psi and lambda.  reg_adjoint_available tells whether this state takes
 // it (mode, size); run_adjoint_compiled launches all segments, writing the
-// per-slot partial sums of Im<lambda|G|psi> (slot_op: the op of each slot).
+// per-slot partial sums of Im<lambda|G|psi> (slot_op: the op of each slot;
+// slot_scale: the factor each slot's summed partials take).  Returns
+// LQS_ERR_UNSUPPORTED, having launched nothing, when the interpreter must run.
 bool reg_adjoint_available(const SV* sv, int arith);
 int adjoint_tile_qubits(int dtype);  // tile of the compiled reverse sweep
 int run_adjoint_compiled(SV* sv, const std::vector<KOp>& rev, void* lam, int arith, std::vector<int>& slot_op,
-                         double** partial, int* grid);
+                         std::vector<double>& slot_scale, double** partial, int* grid);
 // Host only: compile the reverse sweep's kernels (rev = inverse ops, reversed).
 int adjoint_precompile(int n, int dtype, int arith, const std::vector<KOp>& rev, int* compiled);
 // Segment compiler hooks: note_reg_prog builds a segment's register-tile

@@ -567,7 +567,8 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint(typename A::S* __restr
 // block per slot), brings them to the host and adds gen_scale * sum to the
 // gradient of each slot's parameter.
 static int adjoint_finish(SV* sv, const std::vector<KOp>& rev, double* partial, int grid,
-                          const std::vector<int>& slot_owner, int n_params, double* grads) {
+                          const std::vector<int>& slot_owner, int n_params, double* grads,
+                          const std::vector<double>* slot_scale = nullptr) {
   const size_t nslots = slot_owner.size();
   double* sums = partial + nslots * (size_t)grid;
   if (nslots) {
@@ -587,7 +588,8 @@ static int adjoint_finish(SV* sv, const std::vector<KOp>& rev, double* partial, 
   }
   for (size_t s = 0; s < nslots; ++s) {
     const KOp& o = rev[slot_owner[s]];
-    if (o.param_slot < n_params) grads[o.param_slot] += o.gen_scale * h[s];
+    const double sc = slot_scale && s < slot_scale->size() ? (*slot_scale)[s] : 1.0;
+    if (o.param_slot < n_params) grads[o.param_slot] += o.gen_scale * sc * h[s];
   }
   return LQS_OK;
 }
@@ -620,11 +622,12 @@ static int adjoint_t(SV* sv, const std::vector<KOp>& ops, int n_params, const lq
   if (reg_adjoint_available(sv, 0)) {
     // compiled reverse sweep: register-tile programs over psi and lambda
     std::vector<int> slot_op;
+    std::vector<double> slot_scale;
     double* partial = nullptr;
     int grid = 0;
     const int ar = std::is_same<A, ArF64>::value ? LQS_ARITH_F64 : LQS_ARITH_DF;
-    const int rc = run_adjoint_compiled(sv, rev, lam, ar, slot_op, &partial, &grid);
-    if (rc == LQS_OK) return adjoint_finish(sv, rev, partial, grid, slot_op, n_params, grads);
+    const int rc = run_adjoint_compiled(sv, rev, lam, ar, slot_op, slot_scale, &partial, &grid);
+    if (rc == LQS_OK) return adjoint_finish(sv, rev, partial, grid, slot_op, n_params, grads, &slot_scale);
     if (rc != LQS_ERR_UNSUPPORTED) return rc;  // nothing was launched when it is unsupported
   }
   PlanCfg pc;

@@ -150,6 +150,39 @@ def test_compiled_adjoint_all_parametrised_gates(jit_on, dtype, arith):
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("with_pi", [False, True])
+def test_compiled_adjoint_edge_angles(jit_on, dtype, arith, with_pi):
+    """The double-float sweep un-applies RY and H as m00 times a matrix with a
+    unit diagonal, so psi and lambda grow by 1/m00 inside a segment and the
+    gradient partials come out scaled.  Angles where m00 is small (near pi),
+    at the tie |cos| = |sin|, negative and beyond 2 pi; with an angle of
+    exactly pi the segment's pivot product leaves float32 range and the
+    interpreter sweep runs instead.  Gradients against the oracle's
+    parameter shift either way."""
+    set_mode(arith)
+    n = 13
+    angles = [np.pi - 1e-3, -(np.pi - 2e-3), np.pi / 2, 1.2, -2.9, 3 * np.pi + 0.4, 7.0, 1e-9, 2.0, np.pi - 0.05]
+    if with_pi:
+        angles = angles[:4] + [np.pi] + angles[4:]
+    c = W.Circuit(n)
+    for i, th in enumerate(angles):
+        q = (5 * i) % n
+        c.add("RY", (q,), (th,))
+        c.add("RZ", ((q + 1) % n,), (0.3 + i,))
+        c.add("CNOT", (q, (q + 2) % n))
+        if i % 3 == 0:
+            c.add("H", ((q + 7) % n,))
+    psi0 = W.gaussian_state(n, 515)
+    terms = W.tfim(n) + [W.pauli_word(0.4, {2: "Y", 11: "X"})]
+    g_ref = oracle.param_shift_grad(c, terms, psi0)
+    with gpu_state(n, dtype, psi0) as sv:
+        sv.apply(c, fused=True)
+        g, _ = sv.adjoint_grad(c, terms)
+    tol = 1e-10 if dtype == "c128" else 5e-4
+    np.testing.assert_allclose(g, g_ref, atol=tol)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
 def test_compiled_adjoint_matches_interpreter_sweep(dtype, arith):
     """Same circuit and state: gradients of the compiled sweep (LQS_JIT_ON)
     and of the shared-memory sweep (LQS_JIT_OFF)."""
