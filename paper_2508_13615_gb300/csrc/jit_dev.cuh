@@ -419,6 +419,25 @@ __device__ __forceinline__ void gflush4(float a0, float a1, float a2, float a3, 
   if ((lane & 7u) == 0 && s) *s += (double)k;
 }
 
+// A running sum held by one lane across the tile loop and stored in its
+// slot once: double-float for complex128 kernels, float64 for complex64.
+template <class A> struct LaneAcc {
+  DF s;
+  __device__ __forceinline__ void zero() { s = DF{0.f, 0.f}; }
+  __device__ __forceinline__ void add(const DF& x, bool neg) { s = df_add(s, neg ? df_neg(x) : x); }
+  __device__ __forceinline__ void put(double* slot) const { *reinterpret_cast<DF*>(slot) = s; }
+};
+template <> struct LaneAcc<ArF32> {
+  double s;
+  __device__ __forceinline__ void zero() { s = 0.0; }
+  __device__ __forceinline__ void add(float x, bool neg) { s += neg ? -(double)x : (double)x; }
+  __device__ __forceinline__ void put(double* slot) const { *slot = s; }
+};
+__device__ __forceinline__ DF shfl_idx(const DF& v, uint32_t src) {
+  return DF{__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+__device__ __forceinline__ float shfl_idx(float v, uint32_t src) { return __shfl_sync(0xffffffffu, v, src); }
+
 // Walsh butterfly over the warp: lane l ends with sum_i (-1)^popc(i & l) v_i,
 // so lane 0 holds the plain sum and lane 2^m the sum signed by lane bit m.
 // All 32 lanes must call it.

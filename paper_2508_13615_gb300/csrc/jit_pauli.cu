@@ -57,7 +57,7 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
   const int tb = kPauliThreadBits, r = k - tb, R = 1 << r;
   const bool exp = mode & 1, lam = mode & 2, fresh = mode & 4;
   const int nw = (int)ws.size();
-  std::ostringstream o, pre;
+  std::ostringstream o, pre, post;  // loop body, before the loop, after the loop
   const uint32_t tmask = (1u << tb) - 1u;
   bool need_xa = false;
   for (auto& w : ws)
@@ -119,6 +119,9 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
   if (exp) {
     // diagonal words
     std::map<uint32_t, std::string> walsh;  // register Z pattern -> butterfly result
+    std::vector<std::string> pats;          // butterfly results in order
+    std::map<uint32_t, int> pat_of;         // register Z pattern -> index in pats
+    std::vector<int> dws;                   // the diagonal words
     bool have_p = false;
     for (int w = 0; w < nw; ++w) {
       const JWord& W = ws[w];
@@ -139,11 +142,36 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
         const std::string wn = "D" + std::to_string(uid++);
         o << "    const auto " << wn << " = lqs::jit::wht(" << sn << ");\n";
         it = walsh.emplace(zr, wn).first;
+        pat_of[zr] = (int)pats.size();
+        pats.push_back(wn);
       }
-      // lane bits: the butterfly's lane; warp bits and outside bits: a sign
-      const std::string sg = x_(thread_sign(zt & ~31u), tile_sign(W.ze));
-      o << "    lqs::jit::gput(" << it->second << ", (tid & 31u) == " << (zt & 31u) << "u, " << sg << ", wacc + warp * "
-        << nw << " + " << w << ");\n";
+      (void)zt;
+      dws.push_back(w);
+    }
+    // Each diagonal word's value for this tile sits in the butterfly lane of
+    // its lane Z bits, signed by its warp and outside-tile Z bits.  Diagonal
+    // word k is summed across tiles by lane k mod 32 of every warp (one
+    // shuffle per register pattern and one add for all of them) and stored in
+    // its slot after the tile loop.
+    for (size_t a = 0; 32 * a < dws.size(); ++a) {
+      const std::string A_ = std::to_string(a);
+      pre << "  uint32_t dsrc" << A_ << " = 0u, dpat" << A_ << " = 0u, dzt" << A_ << " = 0u;\n  uint64_t dze" << A_
+          << " = 0ull;\n  int dw" << A_ << " = -1;\n  lqs::jit::LaneAcc<A> dacc" << A_ << ";\n  dacc" << A_
+          << ".zero();\n";
+      for (size_t kk = 0; kk < 32 && 32 * a + kk < dws.size(); ++kk) {
+        const JWord& W = ws[dws[32 * a + kk]];
+        const uint32_t zr = W.zl >> tb, zt = W.zl & tmask;
+        pre << "  if ((tid & 31u) == " << kk << "u) { dsrc" << A_ << " = " << (zt & 31u) << "u; dpat" << A_ << " = "
+            << pat_of[zr] << "u; dzt" << A_ << " = " << (zt & ~31u) << "u; dze" << A_ << " = " << hx(W.ze) << "; dw"
+            << A_ << " = " << dws[32 * a + kk] << "; }\n";
+      }
+      o << "    { auto x = lqs::jit::shfl_idx(" << pats[0] << ", dsrc" << A_ << ");\n";
+      for (size_t i = 1; i < pats.size(); ++i)
+        o << "      { const auto y = lqs::jit::shfl_idx(" << pats[i] << ", dsrc" << A_ << "); if (dpat" << A_
+          << " == " << i << "u) x = y; }\n";
+      o << "      dacc" << A_ << ".add(x, ((__popc(tid & dzt" << A_ << ") + __popcll(base & dze" << A_
+        << ")) & 1) != 0); }\n";
+      post << "  if (dw" << A_ << " >= 0) dacc" << A_ << ".put(wacc + warp * " << nw << " + dw" << A_ << ");\n";
     }
     // X/Y words: pairs with the lowest X bit clear.  Their warp sums go four
     // at a time through one reduce-scatter (gflush4).
@@ -199,6 +227,30 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
             term(val(e ^ (int)xr), "lqs::ld_w(&XA[(tid ^ " + std::to_string(xt) + "u) + " + std::to_string(e << tb) + "u])",
                  neg_at(e, st1));
         o << "      }\n";
+      } else if (!lowreg && r >= 1) {
+        // a lane bit: both lanes of each pair take half of the pairs (split by
+        // the top register bit) in one instruction stream: each lane selects
+        // its register operand and the shared-memory position of the other.
+        // The lower lane holds the representative, the upper lane its
+        // partner; Re(conj(c) b) does not depend on the order of the two,
+        // Im(conj(c) b) changes sign, so the upper lanes flip the imaginary
+        // forms' sign.
+        const int ms = r - 1;
+        const uint32_t xt = W.xl & tmask, xr = W.xl >> tb;
+        const std::string sx = thread_sign(zt);
+        const std::string st1 = x_((__builtin_popcount(xt & zt) & 1) ? "!" + sx : sx, tile_sign(W.ze));
+        const std::string hb = "hb" + std::to_string(uid++);
+        o << "      const bool " << hb << " = ((tid >> " << W.lowbit << ") & 1u) != 0u;\n";
+        for (int i = 0; i < R / 2; ++i) {
+          const int e0 = i, e1 = i | (1 << ms);
+          const std::string rg = "(" + hb + " ? " + val(e1 ^ (int)xr) + " : " + val(e0) + ")";
+          const std::string sm = "lqs::ld_w(&XA[(tid ^ " + std::to_string(xt) + "u) + (" + hb + " ? " +
+                                 std::to_string(e1 << tb) + "u : " + std::to_string((e0 ^ (int)xr) << tb) + "u)])";
+          const std::string nu = neg_at(e1, st1), nl = neg_at(e0, st);
+          const std::string ng = (W.ph & 1) ? "(" + hb + " ? !(" + nu + ") : " + nl + ")"
+                                             : "(" + hb + " ? " + nu + " : " + nl + ")";
+          term(sm, rg, ng);
+        }
       } else {
         if (!lowreg) o << "      if (!((tid >> " << W.lowbit << ") & 1u)) {\n";
         for (int e = 0; e < R; ++e) {
@@ -259,9 +311,9 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
         << ");\n";
     for (int m = 0; m < r; ++m) pre << "  const uint64_t st_" << m << " = 1ull << G.h[" << (tb + m - b) << "];\n";
   }
-  const std::string body = o.str(), prel = pre.str();
+  const std::string body = o.str(), prel = pre.str(), postl = post.str();
   uint64_t h = 1469598103934665603ull;
-  for (unsigned char ch : body + prel + aname) h = (h ^ ch) * 1099511628211ull;
+  for (unsigned char ch : body + prel + postl + aname) h = (h ^ ch) * 1099511628211ull;
   char nm[40];
   std::snprintf(nm, sizeof nm, "lqs_pauli_%016llx", (unsigned long long)(h ^ ((uint64_t)mode << 56)));
   kname = nm;
@@ -302,7 +354,7 @@ std::string pauli_source(const char* aname, int k, int b, const std::vector<JWor
        "    ok = __syncthreads_and(lqs::mbar_wait(bar, phase));\n"
        "    phase ^= 1u;\n    if (!ok) break;\n"
     << "    if (tid == 0 && t + gridDim.x < G.ntiles) lqs::jit::seg_expect(G, bar, " << (two_in ? 2 : 1) << "u);\n"
-    << body << "  }\n"
+    << body << "  }\n" << postl
     << "  if (!ok && tid == 0) {\n    lqs::flag_timeout(status, 2);\n    lqs::mbar_wait(bar, phase ^ 1u);\n  }\n"
        "  __syncthreads();\n"
     << "  for (int w = tid; w < " << nw << "; w += blockDim.x) {\n"
