@@ -82,7 +82,7 @@ def test_named_barriers_are_never_shared(tmp_path, monkeypatch):
     for f in files:
         src = open(f).read()
         nthreads = int(re.search(r"__launch_bounds__\((\d+),", src).group(1))
-        body = src.split("for (; t < G.ntiles; t += gridDim.x) {", 1)[1]
+        body = re.split(r"for \(; t < G\.ntiles; t \+= [^)]*\) \{", src, maxsplit=1)[1]
         used = set()
         for line in body.splitlines():
             if "__syncthreads" in line:
@@ -197,7 +197,7 @@ def _unordered_accesses(src):
 
     nth = int(re.search(r"__launch_bounds__\((\d+),", src).group(1))
     nw = nth // 32
-    body = src.split("for (; t < G.ntiles; t += gridDim.x) {", 1)[1]
+    body = re.split(r"for \(; t < G\.ntiles; t \+= [^)]*\) \{", src, maxsplit=1)[1]
     events = []  # ("bar", key(warp)) or ("acc", buf, is_write, {position: warp})
     jt = named = None
     named = {}
