@@ -174,6 +174,10 @@ class SegGen {
   // gradient partials (seg_scales) and folds into a diagonal run or a final
   // scale; launches whose product of m00's is too small run elsewhere.
   bool unit_adj() const { return adj_ && aname_ == std::string("lqs::ArDF"); }
+  // Complex64 forward segments do too little arithmetic per tile to hide a
+  // tile load behind it: they keep two incoming buffers (two tiles in flight
+  // per CTA) and run every layout exchange through one buffer.
+  bool deep() const { return !adj_ && aname_ == std::string("lqs::ArF32"); }
   void flush_pending(bool all);
   // runs f once per state, with V() naming that state's variables
   template <class F>
@@ -547,7 +551,7 @@ void SegGen::emit_layout(const TOp& t) {
   each([&]() {
     const int xi = xb_;
     const char* X = xb_ ? "XB" : "XA";
-    xb_ ^= 1;
+    if (!deep()) xb_ ^= 1;  // deep: XA only (the second incoming buffer took XB's place)
     std::copy(saved_slot, saved_slot + 4, slot_);  // barrier groups compare with the current layout
     std::copy(saved_thr, saved_thr + 16, thr_);
     bool unsafe = !exchange_safe(xi, wown);
@@ -1155,6 +1159,57 @@ extern "C" __global__ void __launch_bounds__(@NTH@, @MINB@)
     if (tid == 0 && t + gridDim.x < G.ntiles) lqs::jit::seg_expect(G, bar, @NSTATES@);
 )";
 
+// Complex64 forward segments: two incoming buffers and two barriers; tile
+// it of this CTA lands in buffer it & 1 (barrier phase (it >> 1) & 1).
+const char* kSkeletonHeadDeep = R"(
+extern "C" __global__ void __launch_bounds__(@NTH@, @MINB@)
+@NAME@(A::S* __restrict__ psi, const __grid_constant__ SegArgs P, int* status, const unsigned fmt) {
+  typedef A::S S;
+  typedef A::W W;
+  typedef A::C C;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const lqs::TileGeom& G = P.g;
+  S* S0 = reinterpret_cast<S*>(smem_raw);      // incoming tiles, two buffers (two tiles in flight)
+  W* XA = reinterpret_cast<W*>(S0 + @NT@ * 2u);  // every layout exchange
+  W* XB = XA;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(XA + @NT@);
+  const uint32_t tid = threadIdx.x;
+  (void)XB;
+  (void)fmt;
+  uint64_t t = blockIdx.x;
+  const uint64_t grid = gridDim.x;
+  if (tid == 0) {
+    lqs::mbar_init(bar, 1);
+    lqs::mbar_init(bar + 1, 1);
+    lqs::fence_mbar_init();
+    if (t < G.ntiles) lqs::jit::seg_expect(G, bar, 1u);
+    if (t + grid < G.ntiles) lqs::jit::seg_expect(G, bar + 1, 1u);
+  }
+  __syncthreads();
+  const uint64_t my_roff = tid < (1u << G.r) ? lqs::row_offset(G, tid) : 0ull;
+  if (t < G.ntiles) lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, t), bar, my_roff);
+  if (t + grid < G.ntiles) lqs::jit::seg_copy(G, S0 + @NT@, psi, lqs::tile_base(G, t + grid), bar + 1, my_roff);
+  uint32_t it = 0;
+  bool ok = true;
+@TBL@@PRE@  for (; t < G.ntiles; t += grid, ++it) {
+    const uint64_t base = lqs::tile_base(G, t);
+    S* SIN = S0 + @NT@ * (it & 1u);
+    uint64_t* BAR = bar + (it & 1u);
+    ok = __syncthreads_and(lqs::mbar_wait(BAR, (it >> 1) & 1u));
+    if (!ok) break;
+    // the byte count of this buffer's next tile goes up before its copies are issued
+    if (tid == 0 && t + 2ull * grid < G.ntiles) lqs::jit::seg_expect(G, BAR, 1u);
+)";
+
+const char* kSkeletonTailDeep = R"(  }
+  if (!ok && tid == 0) {
+    lqs::flag_timeout(status, 4);
+    lqs::mbar_wait(bar + (it & 1u), (it >> 1) & 1u);  // let the copies in flight land (bounded)
+    if (t + grid < G.ntiles) lqs::mbar_wait(bar + ((it + 1u) & 1u), ((it + 1u) >> 1) & 1u);
+  }
+}
+)";
+
 const char* kSkeletonTail = R"(  }
   if (!ok && tid == 0) {
     lqs::flag_timeout(status, 4);
@@ -1223,26 +1278,33 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     o_ << "    W";
     for (int e = 0; e < R_; ++e) o_ << (e ? ", " : " ") << pfx_ << e;
     o_ << ";\n";
+    const char* sin = pfx_[0] == 'v' ? (deep() ? "SIN" : "S0") : "S0L";
     if (split_io()) {  // the previous segment of this call left hi/lo pairs
       o_ << "    if (fmt & 1u) {\n";
       for (int e = 0; e < R_; ++e)
-        o_ << "      " << pfx_ << e << " = lqs::ld_w(reinterpret_cast<const W*>(" << (pfx_[0] == 'v' ? "S0" : "S0L")
-           << " + (jt + " << hex32(je(e)) << ")));\n";
+        o_ << "      " << pfx_ << e << " = lqs::ld_w(reinterpret_cast<const W*>(" << sin << " + (jt + " << hex32(je(e))
+           << ")));\n";
       o_ << "    } else {\n";
     }
     for (int e = 0; e < R_; ++e)
-      o_ << (split_io() ? "  " : "") << "    " << pfx_ << e << " = A::load(" << (pfx_[0] == 'v' ? "S0" : "S0L")
-         << "[jt + " << hex32(je(e)) << "]);\n";
+      o_ << (split_io() ? "  " : "") << "    " << pfx_ << e << " = A::load(" << sin << "[jt + " << hex32(je(e))
+         << "]);\n";
     if (split_io()) o_ << "    }\n";
   });
   if (logical != through) {
     set_layout(logical);
     o_ << "    jt = " << jt_expr() << ";\n";
   }
-  o_ << "    __syncthreads();  // the incoming buffers are free: prefetch the next tile into them\n"
-        "    { const uint64_t tn = t + gridDim.x;\n"
-        "      if (tn < G.ntiles) {\n"
-        "        lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, tn), bar, my_roff);\n";
+  if (deep())
+    o_ << "    __syncthreads();  // this incoming buffer is free: the tile two ahead goes into it\n"
+          "    { const uint64_t tn = t + 2ull * gridDim.x;\n"
+          "      if (tn < G.ntiles) {\n"
+          "        lqs::jit::seg_copy(G, SIN, psi, lqs::tile_base(G, tn), BAR, my_roff);\n";
+  else
+    o_ << "    __syncthreads();  // the incoming buffers are free: prefetch the next tile into them\n"
+          "    { const uint64_t tn = t + gridDim.x;\n"
+          "      if (tn < G.ntiles) {\n"
+          "        lqs::jit::seg_copy(G, S0, psi, lqs::tile_base(G, tn), bar, my_roff);\n";
   if (adj_) o_ << "        lqs::jit::seg_copy(G, S0L, lam, lqs::tile_base(G, tn), bar, my_roff);\n";
   o_ << "      } }\n";
   for (int i = first; i < nops; ++i) {
@@ -1318,7 +1380,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     << "struct SegArgs {\n  lqs::TileGeom g;\n  A::C coef[" << std::max(ncoef, 1) << "];\n";
   if (nu_) s << "  A::C gscale;\n  uint32_t usel[" << (nu_ + 31) / 32 << "];\n";
   s << "};\n";
-  std::string head = replace_all(kSkeletonHead, "@NAME@", kname);
+  std::string head = replace_all(deep() ? kSkeletonHeadDeep : kSkeletonHead, "@NAME@", kname);
   head = replace_all(head, "@NTH@", std::to_string(nth));
   // resident CTAs per SM the register budget aims at: forward 512 threads
   // per SM; adjoint 3 x 128, with 256 threads 2 (4 amplitudes of each state
@@ -1337,7 +1399,7 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
                      adj_ ? "    lqs::jit::seg_copy(G, S0L, lam, lqs::tile_base(G, t), bar, my_roff);\n" : "");
   head = replace_all(head, "@TBL@", ntab_ ? "  __shared__ C TBL[" + std::to_string(ntab_) + "];\n" : std::string());
   head = replace_all(head, "@PRE@", pre_.str());
-  std::string tail = kSkeletonTail;
+  std::string tail = deep() ? kSkeletonTailDeep : kSkeletonTail;
   std::string gout;
   if (adj_) {
     gout = replace_all(kGradOut, "@NGRAD@", std::to_string(ngrad));
@@ -1857,7 +1919,10 @@ int jit_launch(const TileProg<A>& P, int r, SV* sv, double bytes, double flops, 
   Entry* e = entry_for(P, r, false, false, nullptr);
   const int dev = sv->device;
   const int threads = 1 << (P.g.k - r);
-  const size_t smem = 3 * ((size_t)sizeof(typename A::S) << P.g.k) + 16;  // incoming tile, two exchange buffers
+  // incoming tile and two exchange buffers, or (complex64) two incoming
+  // tiles and one exchange buffer; one or two barriers
+  const bool deep = std::is_same<A, ArF32>::value;
+  const size_t smem = 3 * ((size_t)sizeof(typename A::S) << P.g.k) + (deep ? 32 : 16);
   CUfunction fn;
   int per_sm;
   LQS_TRY(entry_function(e, dev, smem, threads, &fn, &per_sm));
