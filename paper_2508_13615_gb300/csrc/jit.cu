@@ -136,6 +136,8 @@ class SegGen {
   std::string why_;
   std::vector<std::pair<std::string, int>> pend_;  // gradient partials awaiting a batched warp sum
   int ntab_ = 0;  // entries of the shared table of outside-qubit factor products
+  int nut_ = 0;   // entries of the shared tables of tile-independent diagonal runs (UT)
+  std::vector<std::string> ofac_;  // per run with outside factors: its per-tile product (OF)
   int lz_ = 0;    // amplitude updates since the registers were last renormalised
   // Exchanges since the last block-wide barrier, for the ordering check of
   // a buffer's next writes (exchange_safe): per exchange its buffer, the warp
@@ -1039,67 +1041,88 @@ bool SegGen::emit_op(const TOp& t) {
       o_ << "    // merged diagonal run\n";
       if (!p.empty()) o_ << "    if (" << p << ") {\n";
       o_ << "    {\n";
-      // C times the factors on this thread's bits: the same for every tile,
-      // so it is formed once per thread before the tile loop
       const uint32_t regpos = reg_positions();
-      std::string h = cref(c);
-      if (LF & ~regpos) {
-        h = fresh("h");
-        pre_ << "  C " << h << " = " << cref(c) << ";\n  { const uint32_t jt = " << jt_expr() << ";\n";
-        for (int q = 0; q < k_; ++q)
-          if (((LF >> q) & 1u) && !((regpos >> q) & 1u))
-            pre_ << "    if ((jt >> " << q << ") & 1u) " << h << " = A::kmul(" << cref(lidx(q)) << ", " << h << ");\n";
-        pre_ << "  }\n";
-      }
-      const std::string a = fresh("a");
-      o_ << "      C " << a << " = " << h << ";\n";
-      // factors on qubits outside the tile depend only on the tile: groups of
-      // up to 4 such qubits get a 16-entry product table in shared memory,
-      // filled once per CTA before the tile loop (its first barrier orders the
-      // fill before any use), so a tile pays one product per group
-      std::vector<std::pair<int, int>> outs;  // (qubit, coefficient index)
-      for (int q = 0, j = 0; q < 64; ++q)
-        if ((EF >> q) & 1ull) outs.emplace_back(q, c + 1 + __builtin_popcount(LF) + j++);
-      for (size_t g0 = 0; g0 < outs.size(); g0 += 4) {
-        const size_t m = std::min<size_t>(4, outs.size() - g0);
-        if (m == 1) {
-          o_ << "      if ((base >> " << outs[g0].first << ") & 1ull) " << a << " = lqs::jit::Lz<A>::kmul(" << cref(outs[g0].second)
-             << ", " << a << ");\n";
-          continue;
-        }
-        const int off = ntab_;
-        ntab_ += 1 << m;
-        pre_ << "  for (uint32_t i = tid; i < " << (1u << m) << "u; i += blockDim.x) {\n    C f = A::cconst1();\n";
-        for (size_t b = 0; b < m; ++b)
-          pre_ << "    if (i & " << (1u << b) << "u) f = A::kmul(" << cref(outs[g0 + b].second) << ", f);\n";
-        pre_ << "    TBL[" << off << "u + i] = f;\n  }\n";
-        std::string ix;
-        for (size_t b = 0; b < m; ++b)
-          ix += std::string(b ? " | " : "") + "((uint32_t)(base >> " + std::to_string(outs[g0 + b].first) + ") & 1u) << " +
-                std::to_string(b);
-        o_ << "      " << a << " = lqs::jit::Lz<A>::kmul(TBL[" << off << "u + (" << ix << ")], " << a << ");\n";
-      }
       uint32_t fmask = 0;  // register slots carrying a factor
       for (int m = 0; m < r_; ++m)
         if ((LF >> slot_[m]) & 1u) fmask |= 1u << m;
+      std::vector<std::pair<int, int>> outs;  // factors on qubits outside the tile: (qubit, coefficient index)
+      for (int q = 0, j = 0; q < 64; ++q)
+        if ((EF >> q) & 1ull) outs.emplace_back(q, c + 1 + __builtin_popcount(LF) + j++);
       std::map<uint32_t, std::string> tab;
-      tab[0] = a;
-      // products for the needed factor patterns, each from a smaller one
       std::vector<uint32_t> need;
       for (int e = 0; e < R_; ++e)
         if (qual(e)) need.push_back((uint32_t)e & fmask);
       std::sort(need.begin(), need.end());
       need.erase(std::unique(need.begin(), need.end()), need.end());
-      std::vector<uint32_t> all;
-      for (uint32_t key : need)
-        for (uint32_t x = key; x; x &= ~(1u << (31 - __builtin_clz(x)))) all.push_back(x);
-      std::sort(all.begin(), all.end());
-      all.erase(std::unique(all.begin(), all.end()), all.end());
-      for (uint32_t key : all) {
-        const int m = 31 - __builtin_clz(key);
-        const std::string nm = fresh("f");
-        o_ << "      const C " << nm << " = lqs::jit::Lz<A>::kmul(" << cref(lidx(slot_[m])) << ", " << tab[key ^ (1u << m)] << ");\n";
-        tab[key] = nm;
+      if (!(LF & ~regpos) && outs.empty()) {
+        // no factor on a thread bit or outside the tile: the whole table is
+        // the same for every thread and tile, formed once per CTA before the
+        // tile loop in shared memory (its first barrier orders the fill)
+        const int u0 = nut_;
+        nut_ += R_;
+        pre_ << "  for (uint32_t i = tid; i < " << R_ << "u; i += blockDim.x) {\n    C f = " << cref(c) << ";\n";
+        for (int m = 0; m < r_; ++m)
+          if ((fmask >> m) & 1u)
+            pre_ << "    if ((i >> " << m << ") & 1u) f = A::kmul(" << cref(lidx(slot_[m])) << ", f);\n";
+        pre_ << "    UT[" << u0 << "u + i] = f;\n  }\n";
+        for (uint32_t key : need) tab[key] = "UT[" + std::to_string(u0 + (int)key) + "u]";
+      } else {
+        // C times the factors on this thread's bits: the same for every tile,
+        // so it is formed once per thread before the tile loop
+        std::string h = cref(c);
+        if (LF & ~regpos) {
+          h = fresh("h");
+          pre_ << "  C " << h << " = " << cref(c) << ";\n  { const uint32_t jt = " << jt_expr() << ";\n";
+          for (int q = 0; q < k_; ++q)
+            if (((LF >> q) & 1u) && !((regpos >> q) & 1u))
+              pre_ << "    if ((jt >> " << q << ") & 1u) " << h << " = A::kmul(" << cref(lidx(q)) << ", " << h << ");\n";
+          pre_ << "  }\n";
+        }
+        const std::string a = fresh("a");
+        o_ << "      C " << a << " = " << h << ";\n";
+        if (!outs.empty()) {
+          // The factors on qubits outside the tile depend only on the tile:
+          // their product is formed once per tile, one tile ahead, by lane 0
+          // of one warp into a double-buffered shared slot (OF), so each
+          // thread pays one product.  Groups of up to 4 qubits read a
+          // 16-entry table filled once per CTA before the tile loop.
+          std::string code;
+          for (size_t g0 = 0; g0 < outs.size(); g0 += 4) {
+            const size_t m = std::min<size_t>(4, outs.size() - g0);
+            if (m == 1) {
+              code += "if ((ob >> " + std::to_string(outs[g0].first) + ") & 1ull) f = A::kmul(" + cref(outs[g0].second) +
+                      ", f); ";
+              continue;
+            }
+            const int off = ntab_;
+            ntab_ += 1 << m;
+            pre_ << "  for (uint32_t i = tid; i < " << (1u << m) << "u; i += blockDim.x) {\n    C f = A::cconst1();\n";
+            for (size_t b = 0; b < m; ++b)
+              pre_ << "    if (i & " << (1u << b) << "u) f = A::kmul(" << cref(outs[g0 + b].second) << ", f);\n";
+            pre_ << "    TBL[" << off << "u + i] = f;\n  }\n";
+            std::string ix;
+            for (size_t b = 0; b < m; ++b)
+              ix += std::string(b ? " | " : "") + "((uint32_t)(ob >> " + std::to_string(outs[g0 + b].first) +
+                    ") & 1u) << " + std::to_string(b);
+            code += "f = A::kmul(TBL[" + std::to_string(off) + "u + (" + ix + ")], f); ";
+          }
+          o_ << "      " << a << " = lqs::jit::Lz<A>::kmul(OF[@OFCUR@ + " << ofac_.size() << "u], " << a << ");\n";
+          ofac_.push_back(code);
+        }
+        tab[0] = a;
+        // products for the needed factor patterns, each from a smaller one
+        std::vector<uint32_t> all;
+        for (uint32_t key : need)
+          for (uint32_t x = key; x; x &= ~(1u << (31 - __builtin_clz(x)))) all.push_back(x);
+        std::sort(all.begin(), all.end());
+        all.erase(std::unique(all.begin(), all.end()), all.end());
+        for (uint32_t key : all) {
+          const int m = 31 - __builtin_clz(key);
+          const std::string nm = fresh("f");
+          o_ << "      const C " << nm << " = lqs::jit::Lz<A>::kmul(" << cref(lidx(slot_[m])) << ", " << tab[key ^ (1u << m)]
+             << ");\n";
+          tab[key] = nm;
+        }
       }
       each([&]() {
         for (int e = 0; e < R_; ++e)
@@ -1363,7 +1386,29 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
     });
   }
   emit_store();  // natural order, or a layout that keeps sectors on lanes
-  const std::string body = o_.str();
+  if (!ofac_.empty()) {
+    // per-tile outside-factor products: the next tile's, after this tile's
+    // last use of the other buffer; the first tile's before the loop (after
+    // a barrier that orders the TBL fill)
+    const int nwarps = nthreads() / 32;
+    const std::string nof = std::to_string(ofac_.size()) + "u";
+    auto fill = [&](std::ostringstream& os, const char* tile, const std::string& slot, const char* ind) {
+      os << ind << "if (" << tile << " < G.ntiles && (tid & 31u) == 0u) {\n" << ind << "  const uint64_t ob = lqs::tile_base(G, "
+         << tile << ");\n" << ind << "  const uint32_t lw = tid >> 5;\n";
+      for (size_t r = 0; r < ofac_.size(); ++r)
+        os << ind << "  if (lw == " << (int)r % nwarps << "u) { C f = A::cconst1(); " << ofac_[r] << "OF[" << slot << " + " << r
+           << "u] = f; }\n";
+      os << ind << "}\n";
+    };
+    o_ << "    { const uint64_t tno = t + gridDim.x;\n";
+    fill(o_, "tno", deep() ? "((it + 1u) & 1u) * " + nof : "phase * " + nof, "      ");
+    o_ << "    }\n";
+    pre_ << "  __syncthreads();\n";
+    fill(pre_, "t", "0u", "  ");
+  }
+  std::string body = replace_all(o_.str(), "@OFCUR@",
+                                 (deep() ? std::string("(it & 1u) * ") : std::string("(phase ^ 1u) * ")) +
+                                     std::to_string(ofac_.size()) + "u");
   const uint64_t h = fnv1a(body) ^ (fnv1a(pre_.str()) * 31u) ^ ((uint64_t)ncoef << 48) ^ ((uint64_t)k_ << 40) ^
                      ((uint64_t)b_ << 36) ^ ((uint64_t)ngrad << 24) ^ (adj_ ? 0x5a5aull : 0ull) ^ fnv1a(aname_);
   char nm[40];
@@ -1397,7 +1442,10 @@ bool SegGen::run(const TOp* ops, int nops, int ncoef, int ngrad, std::string& sr
   head = replace_all(head, "@NWACC@", std::to_string(adj_ ? nwarps * kMaxGradSlotsJit : 0) + "u");
   head = replace_all(head, "@LAMCOPY0@",
                      adj_ ? "    lqs::jit::seg_copy(G, S0L, lam, lqs::tile_base(G, t), bar, my_roff);\n" : "");
-  head = replace_all(head, "@TBL@", ntab_ ? "  __shared__ C TBL[" + std::to_string(ntab_) + "];\n" : std::string());
+  head = replace_all(head, "@TBL@",
+                     (ntab_ ? "  __shared__ C TBL[" + std::to_string(ntab_) + "];\n" : std::string()) +
+                         (nut_ ? "  __shared__ C UT[" + std::to_string(nut_) + "];\n" : std::string()) +
+                         (ofac_.empty() ? std::string() : "  __shared__ C OF[" + std::to_string(2 * ofac_.size()) + "];\n"));
   head = replace_all(head, "@PRE@", pre_.str());
   std::string tail = deep() ? kSkeletonTailDeep : kSkeletonTail;
   std::string gout;
