@@ -71,6 +71,37 @@ def test_compiled_matches_interpreter(dtype, arith):
     check_state(out[L.LQS_JIT_ON], out[L.LQS_JIT_OFF], dtype, 2 * (len(W.ansatz(n, 6, 8).ops) + len(W.qft(n).ops)))
 
 
+def test_compiled_and_interpreted_segments_in_one_call():
+    """Consecutive compiled complex128 segments pass the state to each other as
+    double-float pairs; a segment the interpreter runs in between reads and
+    writes float64.  A circuit whose first part was compiled ahead and whose
+    tail was not (automatic mode compiles a structure at its second use) mixes
+    both kinds in one call: the result against the oracle."""
+    import paper_2508_13615_gb300 as L
+    set_mode("df")
+    n = 20
+    head = W.ansatz(n, 3, 31)
+    c = W.ansatz(n, 3, 31)
+    for i, q in enumerate((3, 11, 17, 6)):  # a tail whose structures nothing else compiles
+        c.add("CRY", (q, (q + 9) % n), (0.4 + i,))
+        c.add("Rot", ((q + 4) % n,), (0.1 * i, 0.7, -0.3))
+        c.add("RY", ((q + 13) % n,), (1.1 - i,))
+    psi0 = W.gaussian_state(n, 77)
+    old = L.lqs_jit_info()["mode"]
+    try:
+        L.lqs_set_jit(L.LQS_JIT_AUTO)
+        L.lqs_jit_precompile(n, "c128", head.ops, head.params, L.LQS_ARITH_DF)
+        with gpu_state(n, "c128", psi0) as sv:
+            L.lqs_profile_start()
+            sv.apply(c, fused=True)
+            names = [r[0] for r in L.lqs_profile_stop()]
+            got = sv.numpy()
+    finally:
+        L.lqs_set_jit(old)
+    assert names.count("k_fused_reg_jit/df") >= 2 and "k_fused_reg/df" in names, names
+    check_state(got, oracle.run_circuit(c, psi0), "c128", len(c.ops))
+
+
 @pytest.mark.parametrize("dtype,arith", MODES)
 def test_qft_closed_form_compiled(jit_on, dtype, arith):
     set_mode(arith)
