@@ -329,9 +329,9 @@ DENSE_SOURCES = ("paper_2508_13615_gb300/csrc/gate_kernels.cu", "paper_2508_1361
 # entry names the profile summary it comes from and the digest of the sources
 # at capture time; `traffic` is null whenever the sources have changed since.
 TRAFFIC = {
-    "k_fused_reg_jit/df": {"read": 268.582912e6, "write": 207.035136e6, "capture_qubits": 24,
+    "k_fused_reg_jit/df": {"read": 268.580352e6, "write": 207.187968e6, "capture_qubits": 24,
                            "source": "profiles/compiled_segment_ansatz_24q_c128.md",
-                           "files": SEG_SOURCES, "sha": "17111a2e7c46b07d"},
+                           "files": SEG_SOURCES, "sha": "77c0514505be06ea"},
     "k_block_tc": {"read": 537.046528e6, "write": 475.009792e6, "capture_qubits": 26,
                    "source": "profiles/k_block_tc_tf32x3_26q_c64.md", "files": BLOCK_SOURCES, "sha": "38c07247c2d88ac4"},
 }
@@ -405,9 +405,21 @@ def cpu_baseline_sample(psi_host, sweep_calls_circ, budget_s=15.0):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
+    # the same oracle on one thread: one sweep gate
+    oracle.set_threads(1)
+    try:
+        _, c = sweep_calls_circ[done % len(sweep_calls_circ)]
+        t1 = time.perf_counter()
+        oracle.apply_op(psi_host, n, c.ops[0], c.params)
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(th)
     return {"value": done / dt, "unit": UNIT, "cores": th, "kind": "oracle",
             "sample": f"{done} gates of the P1 sweep applied in place to the 30-qubit complex128 state by the CPU "
-                      f"oracle (general matrix update, OpenMP {th} threads), {dt:.1f} s"}
+                      f"oracle (general matrix update, OpenMP {th} threads), {dt:.1f} s",
+            "one_thread": {"value": 1.0 / dt1, "unit": UNIT,
+                           "sample": f"one P1 sweep gate ({c.ops[0].name}) by the same oracle on one thread, "
+                                     f"{dt1:.1f} s"}}
 
 
 def host_state(n: int, pinned: bool):
@@ -775,6 +787,53 @@ def config_universal30(args):
     sv.close()
 
 
+def config_fusedplain30(args):
+    """The three circuit families of the 30-qubit step (P2 ansatz, P3 QFT) and
+    the universal circuit of Sec. 3.2, complex128: the fused path (compiled
+    segments) against the plain per-gate path, with the HBM passes of each
+    (plain: one kernel launch per lowered gate)."""
+    import torch
+    import paper_2508_13615_gb300 as L
+    n = args.n
+    L.lqs_set_jit(L.LQS_JIT_ON)
+    sv = L.StateVector(n, "c128")
+    st = torch.cuda.current_stream()
+    rows = []
+    for name, c, basis in (("ansatz_10_layers", W.ansatz(n, 10, 3), 0), ("qft", W.qft(n), W.basis_index(n, 4)),
+                           ("universal", W.universal(n), 1)):
+        L.lqs_jit_precompile(n, "c128", c.ops, c.params, L.LQS_ARITH_DF)
+        ops = L.OpArray(c.ops)
+
+        def run(fused):
+            L.lqs_sv_set_basis(sv.h, basis)
+            if fused:
+                L.lqs_apply_fused(sv.h, ops, c.params, None)
+            else:
+                sv.apply(c, fused=False)
+
+        def t_of(fused, reps):
+            run(fused)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                k0 = L.lqs_kernel_launches()
+                e0, e1 = _events()
+                e0.record(st)
+                run(fused)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append((e0.elapsed_time(e1), L.lqs_kernel_launches() - k0 - 1))  # less the set_basis launch
+            return statistics.median(t for t, _ in ts), ts[-1][1]
+
+        ms_f, launches_f = t_of(True, 3)
+        ms_p, launches_p = t_of(False, 1)
+        rows.append({"circuit": name, "gates": len(c.ops), "fused_ms": ms_f, "fused_launches": launches_f,
+                     "plain_ms": ms_p, "plain_launches": launches_p, "speedup_fused": ms_p / ms_f,
+                     "pass_ratio": launches_p / max(launches_f, 1)})
+    print(json.dumps({"config": "fusedplain30", "n_qubits": n, "dtype": "c128", "rows": rows}), flush=True)
+    sv.close()
+
+
 def config_tcblock30(args):
     """Dense 32x32 blocks on the tensor cores at 30 qubits complex64: one
     block pass (tcgen05 3xTF32) against the same run of gates on the fused
@@ -892,7 +951,8 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="let lqs_autotune_fused pick the tile shapes first (measured: +0.4%% for 45 s of tuning)")
     ap.add_argument("--config", default="main",
-                    choices=["main", "adjoint24", "precision32", "batch256", "sweep30", "tcblock30", "universal30"],
+                    choices=["main", "adjoint24", "precision32", "batch256", "sweep30", "tcblock30", "universal30",
+                             "fusedplain30"],
                     help="secondary measurements (one JSON line each); the default is the headline run")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -904,7 +964,8 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         {"adjoint24": config_adjoint24, "precision32": config_precision32, "batch256": config_batch256,
-         "sweep30": config_sweep30, "tcblock30": config_tcblock30, "universal30": config_universal30}[args.config](args)
+         "sweep30": config_sweep30, "tcblock30": config_tcblock30, "universal30": config_universal30,
+         "fusedplain30": config_fusedplain30}[args.config](args)
         return
 
     import torch

@@ -55,6 +55,8 @@ namespace lqs {
 // ---------------------------------------------------------------------------
 namespace {
 
+std::string replace_all(std::string s, const std::string& a, const std::string& b);
+
 uint32_t host_swz(uint32_t j, int sz) {
   if (sz == 16) return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9)) & 7u);
   return j ^ (((j >> 4) ^ (j >> 8)) & 15u);
@@ -1081,17 +1083,19 @@ bool SegGen::emit_op(const TOp& t) {
         const std::string a = fresh("a");
         o_ << "      C " << a << " = " << h << ";\n";
         if (!outs.empty()) {
-          // The factors on qubits outside the tile depend only on the tile:
-          // their product is formed once per tile, one tile ahead, by lane 0
-          // of one warp into a double-buffered shared slot (OF), so each
-          // thread pays one product.  Groups of up to 4 qubits read a
-          // 16-entry table filled once per CTA before the tile loop.
-          std::string code;
+          // The factors on qubits outside the tile depend only on the tile.
+          // Groups of up to 4 qubits read a 16-entry table filled once per
+          // CTA before the tile loop; a single qubit is a conditional
+          // product.  With two groups or more, their product is formed once
+          // per tile, one tile ahead, by lane 0 of one warp into a
+          // double-buffered shared slot (OF), so each thread pays one
+          // product instead of one per group.
+          std::vector<std::string> terms;  // one product each, on the tile base `B` into `F`
           for (size_t g0 = 0; g0 < outs.size(); g0 += 4) {
             const size_t m = std::min<size_t>(4, outs.size() - g0);
             if (m == 1) {
-              code += "if ((ob >> " + std::to_string(outs[g0].first) + ") & 1ull) f = A::kmul(" + cref(outs[g0].second) +
-                      ", f); ";
+              terms.push_back("if ((@B@ >> " + std::to_string(outs[g0].first) + ") & 1ull) @F@ = A::kmul(" +
+                              cref(outs[g0].second) + ", @F@);");
               continue;
             }
             const int off = ntab_;
@@ -1102,12 +1106,18 @@ bool SegGen::emit_op(const TOp& t) {
             pre_ << "    TBL[" << off << "u + i] = f;\n  }\n";
             std::string ix;
             for (size_t b = 0; b < m; ++b)
-              ix += std::string(b ? " | " : "") + "((uint32_t)(ob >> " + std::to_string(outs[g0 + b].first) +
+              ix += std::string(b ? " | " : "") + "((uint32_t)(@B@ >> " + std::to_string(outs[g0 + b].first) +
                     ") & 1u) << " + std::to_string(b);
-            code += "f = A::kmul(TBL[" + std::to_string(off) + "u + (" + ix + ")], f); ";
+            terms.push_back("@F@ = A::kmul(TBL[" + std::to_string(off) + "u + (" + ix + ")], @F@);");
           }
-          o_ << "      " << a << " = lqs::jit::Lz<A>::kmul(OF[@OFCUR@ + " << ofac_.size() << "u], " << a << ");\n";
-          ofac_.push_back(code);
+          if (terms.size() == 1) {
+            o_ << "      " << replace_all(replace_all(terms[0], "@B@", "base"), "@F@", a) << "\n";
+          } else {
+            std::string code;
+            for (const std::string& tm : terms) code += replace_all(replace_all(tm, "@B@", "ob"), "@F@", "f") + " ";
+            o_ << "      " << a << " = lqs::jit::Lz<A>::kmul(OF[@OFCUR@ + " << ofac_.size() << "u], " << a << ");\n";
+            ofac_.push_back(code);
+          }
         }
         tab[0] = a;
         // products for the needed factor patterns, each from a smaller one
