@@ -329,9 +329,9 @@ DENSE_SOURCES = ("paper_2508_13615_gb300/csrc/gate_kernels.cu", "paper_2508_1361
 # entry names the profile summary it comes from and the digest of the sources
 # at capture time; `traffic` is null whenever the sources have changed since.
 TRAFFIC = {
-    "k_fused_reg_jit/df": {"read": 268.580352e6, "write": 207.187968e6, "capture_qubits": 24,
+    "k_fused_reg_jit/df": {"read": 268.581632e6, "write": 207.311360e6, "capture_qubits": 24,
                            "source": "profiles/compiled_segment_ansatz_24q_c128.md",
-                           "files": SEG_SOURCES, "sha": "77c0514505be06ea"},
+                           "files": SEG_SOURCES, "sha": "532d9ed60565e781"},
     "k_block_tc": {"read": 537.046528e6, "write": 475.009792e6, "capture_qubits": 26,
                    "source": "profiles/k_block_tc_tf32x3_26q_c64.md", "files": BLOCK_SOURCES, "sha": "38c07247c2d88ac4"},
 }

@@ -65,14 +65,23 @@ uint32_t host_swz(uint32_t j, int sz) {
 // An exchange's swizzle: swz<sz> with the bank bits of some positions
 // changed.  dm[b] lists the positions whose contribution to bank bit b
 // flips (jit_dev.cuh pfold); all zero is swz<sz> itself.
+//
+// The additive form (add) has no swz<sz> base: the bank bits of position j
+// are its own low bits changed by the parities in dm, and dm names only
+// positions that are thread bits in both layouts of the exchange and changes
+// only bank bits that are not register positions.  The swizzled index of a
+// thread's amplitude is then its thread part's swizzled index plus its
+// register part unchanged (disjoint bits), so each access adds a constant
+// offset to one per-thread index instead of XORing it.
 struct XSwz {
   uint32_t dm[4] = {0, 0, 0, 0};
+  bool add = false;
   bool plain() const { return !(dm[0] | dm[1] | dm[2] | dm[3]); }
 };
 uint32_t host_xswz(uint32_t j, int sz, const XSwz& x) {
   uint32_t f = 0;
   for (int b = 0; b < 4; ++b) f |= (uint32_t)(__builtin_popcount(j & x.dm[b]) & 1) << b;
-  return host_swz(j, sz) ^ f;
+  return (x.add ? j : host_swz(j, sz)) ^ f;
 }
 
 constexpr int kMaxGradSlotsJit = 128;  // gradient slots per compiled adjoint segment
@@ -221,7 +230,11 @@ class SegGen {
   std::string pred(uint32_t lc, uint64_t ec, uint32_t& regc) const;
   std::string barrier_for(uint64_t to, uint32_t* gmask);
   bool emit_op(const TOp& t);
-  XSwz pick_swizzle(const uint32_t* wv, const uint32_t* rv) const;
+  XSwz pick_swizzle(const uint32_t* wv, const uint32_t* rv, uint32_t regmask) const;
+  // "sj ^ c" or, for an additive swizzle, "sj + c": one access of an exchange
+  std::string xacc(const XSwz& xs, uint32_t pos) const {
+    return std::string(xs.add ? "sj + " : "sj ^ ") + hex32(host_xswz(pos, sz_, xs));
+  }
   std::string swz_expr(const std::string& j, const XSwz& x) const;
   bool emit_grad(const TOp& t);
   bool emit_grad_block(const TOp* ops, int count);
@@ -326,12 +339,63 @@ std::string SegGen::barrier_for(uint64_t to, uint32_t* gmask) {
 // exchange re-assigns the fold of the higher lane positions when it must
 // (a small backtracking search), writes and reads through that swizzle, and
 // leaves every other exchange on the default.
-XSwz SegGen::pick_swizzle(const uint32_t* wv, const uint32_t* rv) const {
+XSwz SegGen::pick_swizzle(const uint32_t* wv, const uint32_t* rv, uint32_t regmask) const {
   // wv / rv: the position vectors of the lane bits of the writing and the
-  // reading layout (single positions, or their images under a fold)
+  // reading layout (single positions, or their images under a fold);
+  // regmask: the register positions of both layouts (0: no additive form)
   const int nb = sz_ == 16 ? 3 : 4;
   XSwz x;
   if (k_ - r_ < nb) return x;
+  if (regmask) {
+    // the additive form: bank bits are the low position bits, changed only
+    // by positions that are thread bits in both layouts, and never on a bank
+    // bit that is a register position
+    const uint32_t okb = ((1u << nb) - 1u) & ~regmask;
+    uint32_t ga[16];
+    for (int p = 0; p < 16; ++p) ga[p] = p < nb ? 1u << p : 0u;
+    auto bank_a = [&](uint32_t v) {
+      uint32_t y = 0;
+      for (int p = 0; v; ++p, v >>= 1)
+        if (v & 1u) y ^= ga[p];
+      return y;
+    };
+    auto rank_a = [&](const uint32_t* vec) {
+      uint32_t span = 1u;
+      for (int i = 0; i < nb; ++i) {
+        const uint32_t v = bank_a(vec[i]);
+        uint32_t next = span;
+        for (uint32_t u = 0; u < (1u << nb); ++u)
+          if ((span >> u) & 1u) next |= 1u << (u ^ v);
+        span = next;
+      }
+      return span == (nb == 3 ? 0xFFu : 0xFFFFu);
+    };
+    std::vector<int> fp;  // thread positions above the bank bits met by a lane vector
+    for (int i = 0; i < nb; ++i)
+      for (uint32_t v : {wv[i], rv[i]})
+        for (int p = nb; p < k_; ++p)
+          if (((v >> p) & 1u) && !((regmask >> p) & 1u) && std::find(fp.begin(), fp.end(), p) == fp.end())
+            fp.push_back(p);
+    std::function<bool(size_t)> search_a = [&](size_t i) {
+      if (i == fp.size()) return rank_a(wv) && rank_a(rv);
+      const int p = fp[i];
+      for (uint32_t v = 0; v < (1u << nb); ++v) {
+        if (v & ~okb) continue;
+        ga[p] = v;
+        if (search_a(i + 1)) return true;
+      }
+      ga[p] = 0;
+      return false;
+    };
+    if (search_a(0)) {
+      x.add = true;
+      for (int p = nb; p < k_; ++p)
+        for (int bb = 0; bb < nb; ++bb)
+          if ((ga[p] >> bb) & 1u) x.dm[bb] |= 1u << p;
+      return x;
+    }
+    x = XSwz();
+  }
   auto dflt = [&](int p) { return host_swz(1u << p, sz_) & ((1u << nb) - 1u); };  // bank bits of swz<sz>
   uint32_t g[16];
   for (int p = 0; p < 16; ++p) g[p] = dflt(p);
@@ -378,7 +442,7 @@ XSwz SegGen::pick_swizzle(const uint32_t* wv, const uint32_t* rv) const {
 }
 
 std::string SegGen::swz_expr(const std::string& j, const XSwz& x) const {
-  std::string e = "lqs::jit::swz<" + std::to_string(sz_) + ">(" + j + ")";
+  std::string e = x.add ? j : "lqs::jit::swz<" + std::to_string(sz_) + ">(" + j + ")";
   if (x.plain()) return e;
   return e + " ^ lqs::jit::pfold(" + j + ", " + hex32(x.dm[0]) + ", " + hex32(x.dm[1]) + ", " + hex32(x.dm[2]) +
          ", " + hex32(x.dm[3]) + ")";
@@ -468,7 +532,12 @@ void SegGen::emit_layout(const TOp& t) {
     const int q = r_ + i < k_ ? (int)((t.ecmask >> (4 * (r_ + i))) & 15u) : 0;
     rv[i] = 1u << q;
   }
-  const XSwz xs = pick_swizzle(wv, rv);
+  uint32_t regmask = 0;  // register positions of the writing and the reading layout (none with a fold)
+  if (!F) {
+    regmask = reg_positions();
+    for (int m = 0; m < r_; ++m) regmask |= 1u << ((t.ecmask >> (4 * m)) & 15u);
+  }
+  const XSwz xs = pick_swizzle(wv, rv, regmask);
   // the thread's write index: jt itself, or F jt ^ c (c from the tile's outside bits)
   std::string wj = "jt";
   if (F) {
@@ -531,8 +600,7 @@ void SegGen::emit_layout(const TOp& t) {
       pfx_ = pf;
       for (int e = 0; e < R_; ++e) {
         const uint32_t pos = F ? fold_lin(*F, old_je[e]) : old_je[e];
-        o_ << "      lqs::st_w(&" << (pf[0] == 'v' ? XP : XL) << "[sj ^ " << hex32(host_xswz(pos, sz_, xs)) << "], "
-           << V(e) << ");\n";
+        o_ << "      lqs::st_w(&" << (pf[0] == 'v' ? XP : XL) << "[" << xacc(xs, pos) << "], " << V(e) << ");\n";
       }
     }
     pfx_ = "v";
@@ -542,8 +610,7 @@ void SegGen::emit_layout(const TOp& t) {
     o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
     for (const char* pf : {"v", "u"})
       for (int e = 0; e < R_; ++e)
-        o_ << "      " << pf << e << " = lqs::ld_w(&" << (pf[0] == 'v' ? XP : XL) << "[sj ^ "
-           << hex32(host_xswz(je(e), sz_, xs)) << "]);\n";
+        o_ << "      " << pf << e << " = lqs::ld_w(&" << (pf[0] == 'v' ? XP : XL) << "[" << xacc(xs, je(e)) << "]);\n";
     o_ << "    }\n";
     for (int e = 0; e < R_; ++e) vm_[e] = e;
     if (t.e0 != t.ecmask) {
@@ -582,7 +649,7 @@ void SegGen::emit_layout(const TOp& t) {
     else o_ << "    { const uint32_t sj = " << swz_expr(wj, xs) << ";\n";
     for (int e = 0; e < R_; ++e) {
       const uint32_t pos = F ? fold_lin(*F, old_je[e]) : old_je[e];
-      o_ << "      lqs::st_w(&" << X << "[sj ^ " << hex32(host_xswz(pos, sz_, xs)) << "], " << V(e) << ");\n";
+      o_ << "      lqs::st_w(&" << X << "[" << xacc(xs, pos) << "], " << V(e) << ");\n";
     }
     o_ << "    }\n    " << bar << "\n";
     set_layout(t.ecmask);  // validated by the caller
@@ -590,7 +657,7 @@ void SegGen::emit_layout(const TOp& t) {
     first = false;
     o_ << "    { const uint32_t sj = " << swz_expr("jt", xs) << ";\n";
     for (int e = 0; e < R_; ++e)
-      o_ << "      " << pfx_ << e << " = lqs::ld_w(&" << X << "[sj ^ " << hex32(host_xswz(je(e), sz_, xs)) << "]);\n";
+      o_ << "      " << pfx_ << e << " = lqs::ld_w(&" << X << "[" << xacc(xs, je(e)) << "]);\n";
     o_ << "    }\n";
   });
   for (int e = 0; e < R_; ++e) vm_[e] = e;

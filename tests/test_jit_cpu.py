@@ -153,7 +153,8 @@ def _bank_model(src):
             sj = m.group(1)
             continue
         if sj and ("st_w(&" in s or "ld_w(&" in s):
-            c = int(re.search(r"sj \^ (0x[0-9a-f]+)u", s).group(1), 16)
+            mc = re.search(r"sj (\^|\+) (0x[0-9a-f]+)u", s)
+            op, c = mc.group(1), int(mc.group(2), 16)
             for ph in range(32 // per):
                 groups = {}
                 for lane in range(per * ph, per * (ph + 1)):
@@ -161,7 +162,7 @@ def _bank_model(src):
                     for nm, (ex, jt_then) in named.items():  # each under the jt of its own definition
                         env[nm] = eval(py(ex), dict(env, jt=eval(py(jt_then), {"tid": lane})))
                     env["jt"] = eval(py(jt), {"tid": lane})
-                    a = eval(py(sj), env) ^ c
+                    a = eval(py(sj), env) + c if op == "+" else eval(py(sj), env) ^ c
                     groups[a % per] = groups.get(a % per, 0) + 1
                 extra += max(groups.values()) - 1
         elif sj and s.startswith("}"):
@@ -218,14 +219,14 @@ def _unordered_accesses(src):
             sj = [ev(m.group(1), jt=jt[t], **{k: v[t] for k, v in named.items()}) for t in range(nth)]
             cur = None
             continue
-        m = re.search(r"(st_w|ld_w)\(&(X[ABCD])\[sj \^ (0x[0-9a-f]+)u\]", s)
+        m = re.search(r"(st_w|ld_w)\(&(X[ABCD])\[sj (\^|\+) (0x[0-9a-f]+)u\]", s)
         if m and sj is not None:
-            wr, buf, c = m.group(1) == "st_w", m.group(2), int(m.group(3), 16)
+            wr, buf, op, c = m.group(1) == "st_w", m.group(2), m.group(3), int(m.group(4), 16)
             if cur is None or cur[1] != buf or cur[2] != wr:
                 cur = ["acc", buf, wr, {}]
                 events.append(cur)
             for t in range(nth):
-                cur[3][sj[t] ^ c] = t // 32
+                cur[3][sj[t] + c if op == "+" else sj[t] ^ c] = t // 32
             continue
         if s.startswith("}"):
             sj = None
