@@ -343,7 +343,8 @@ LQS_API int lqs_batch_autotune(const lqs_batch_item* items, int n_items, int dty
  * must belong to the current device (LQS_ERR_ARG otherwise), and the call is
  * synchronous: it copies the results to *out_host (and per_term_host[0..n_terms),
  * if given) and waits for the stream, so it cannot run on a stream that is
- * being captured into a CUDA graph.  n_terms = 0 gives 0.  It calls no
+ * being captured into a CUDA graph: there it returns LQS_ERR_ARG before
+ * enqueuing any work, and the capture stays valid.  n_terms = 0 gives 0.  It calls no
  * cudaMalloc/cudaFree and no allocating library routine: partial sums live in
  * a fixed scratch array compiled into the library (64 terms x 1024 blocks of
  * float64, about 513 KiB), which every GPU that loads the library keeps until

@@ -9,7 +9,8 @@
 // them: it needs no handle and uses a fixed scratch array compiled into the
 // library instead of cudaMalloc.  It is synchronous: it ends by copying the
 // results to host memory and waiting for its stream, so it cannot be called
-// on a stream that is being captured into a CUDA graph.
+// on a stream that is being captured into a CUDA graph: on such a stream it
+// returns LQS_ERR_ARG before enqueuing anything, leaving the capture intact.
 //
 // The scratch array is a file-scope __device__ variable, so every GPU that
 // loads the library holds it until the process exits.  In host code its name
@@ -168,6 +169,14 @@ extern "C" int lqs_expval_static(const void* psi_device, int n_qubits, int dtype
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int sms = 0, dev = 0, sdev = 0;
   LQS_CUDA_TRY(cudaGetDevice(&dev));
+  // The call ends with a copy to pageable host memory and a stream
+  // synchronisation, neither of which a graph capture admits: refuse before
+  // anything is enqueued, so the caller's capture stays valid.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  LQS_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(LQS_ERR_ARG, "lqs_expval_static is synchronous and cannot run on a stream that is being "
+                                  "captured into a CUDA graph; call it outside the capture");
   LQS_CUDA_TRY(cudaStreamGetDevice(st, &sdev));
   if (sdev != dev)
     return set_error(LQS_ERR_ARG, "cuda_stream belongs to device " + std::to_string(sdev) +

@@ -90,3 +90,35 @@ def test_static_expval_rejects_too_many_terms():
         # the state is untouched and a valid call still works
         val, per = L.lqs_expval_static(ptr, n, "c128", [W.pauli_word(1.0, {0: "Z"})])
         assert val == pytest.approx(1.0, abs=1e-15) and per[0] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_static_expval_refuses_a_capturing_stream():
+    """On a stream being captured into a CUDA graph the call must refuse
+    (LQS_ERR_ARG) before it enqueues anything, so that the capture survives
+    and replays; on the same stream outside the capture it works."""
+    import torch
+
+    import paper_2508_13615_gb300 as L
+    from paper_2508_13615_gb300 import lqs as B
+    n = 10
+    terms = [W.pauli_word(1.0, {0: "Z"}), W.pauli_word(0.5, {3: "X"})]
+    with L.StateVector(n, "c128") as sv:
+        sv.set_basis(0)
+        ptr, _, code = L.lqs_sv_info(sv.h)
+        pa = B.PauliArray(terms)
+        lib = ctypes.CDLL(B.LIB_PATH)
+        lib.lqs_expval_static.restype = ctypes.c_int
+        s = torch.cuda.Stream()
+        y = torch.ones(256, device="cuda")
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            rc, _, _ = _call(lib, ptr, n, code, s.cuda_stream, pa)
+            y.mul_(2.0)
+        assert rc == B.LQS_ERR_ARG and "captured" in L.lqs_last_error()
+        g.replay()
+        torch.cuda.synchronize()
+        assert float(y[0]) == 2.0  # recorded, not run, while capturing; run once by the replay
+        rc, e, per = _call(lib, ptr, n, code, s.cuda_stream, pa)
+        assert rc == 0, L.lqs_last_error()
+        assert e == pytest.approx(1.0, abs=1e-14) and per[1] == pytest.approx(0.0, abs=1e-14)
